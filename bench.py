@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: edges colored per second and colors used on R-MAT-B scale 24.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full coloring (gc_color through the C ABI: setup scan, round 1,
+every later round until the worklist is empty) of the synthetic R-MAT-B graph
+(scale 24, edge factor 8, quadrant probabilities (0.55, 0.15, 0.15, 0.15),
+seed 3, ids permuted), with the graph already resident in HBM.  The L2 is
+flushed (256 MB write) before every step, outside the step's CUDA events.
+Prints one JSON line (rank 0).  Multi-GPU runs color one replica per rank
+("replicas only": the method has no exchange step to shard).
+
+--impl reference times the CPU oracle (plain single-threaded C, test
+infrastructure) on the host cores, on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "edges colored/sec and colors used, R-MAT-B scale 24 on 1 GB300, learned vs plain"
+WORKLOAD = ("R-MAT-B scale 24: 16,777,216 vertices, edge factor 8, (a,b,c,d)=(0.55,0.15,0.15,0.15), "
+            "seed 3, duplicates and self loops removed, ids permuted; symmetric int32 CSR; "
+            "plain index priority; synchronous rounds")
+SCALE, EF, ABCD, SEED = 24, 8, gg.RMAT_B, 3
+# bounded CPU samples of the same recipe at smaller scale
+CPU_BASELINE_SCALE = 22
+REFERENCE_STEP_SCALE = 20
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) while the timed region runs."""
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not (t0 - 0.15 <= t <= t1 + 0.15):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- oracle leg
+
+def oracle_rate(scale, runs=1):
+    """Single-threaded CPU oracle on R-MAT-B at `scale` (same recipe): edges/s."""
+    import oracle
+    oracle.build()
+    g = gg.rmat(scale, EF, ABCD, SEED)
+    times = []
+    for _ in range(runs):
+        t = time.perf_counter()
+        r = oracle.iterative(g.rowptr, g.colidx)
+        times.append(time.perf_counter() - t)
+    return g, r, times
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    g = gg.rmat(REFERENCE_STEP_SCALE, EF, ABCD, SEED)
+    for _ in range(args.warmup):
+        oracle.iterative(g.rowptr, g.colidx)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle.iterative(g.rowptr, g.colidx)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = g.m * args.steps / total
+    sample = (f"R-MAT-B scale {REFERENCE_STEP_SCALE} (same recipe: edge factor 8, seed 3), "
+              f"{g.m} edges, one full oracle run per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "ncolors": r.ncolors, "rounds": r.rounds,
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- roofline bits
+
+def algorithmic_bytes_rounds(sizes, vols, elem):
+    """Bytes the fused passes k >= 2 must move (one launch of the rounds kernel).
+
+    Per pass over W = U_k: list 4|W| + rowptr pair 8|W| + own color elem|W|
+    + vol(W) * (4 colidx + elem neighbour color) + writes: next color elem|W|
+    + final int32 color 4 per settled vertex + list append 4|U_{k+1}|.
+    """
+    total = 0
+    R = len(sizes)
+    for k in range(2, R + 1):
+        w, vol = int(sizes[k - 1]), int(vols[k - 1])
+        nxt = int(sizes[k]) if k < R else 0
+        total += 4 * w + 8 * w + elem * w + vol * (4 + elem) + elem * w + 4 * (w - nxt) + 4 * nxt
+    return total
+
+
+def load_traffic(kernel_src):
+    """Per-launch DRAM bytes of the rounds kernel from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "rounds_persistent_kernel_rmat_b.md")
+    if not os.path.exists(path):
+        return None
+    want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_sha256") != want:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# -------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import paper_1205_3809_gb300 as gcpkg
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU path)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    gcpkg.library()
+
+    t = time.time()
+    g = gg.rmat(SCALE, EF, ABCD, SEED)
+    log(f"[rank {rank}] graph n={g.n} m={g.m} maxdeg={g.max_degree} generated in {time.time() - t:.1f}s")
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = {"telemetry": 1}
+
+    def step():
+        return gcpkg.color(rp, ci, out=out, options=opts, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        res = step()
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = "GPU-" + str(getattr(props, "uuid", "")) if getattr(props, "uuid", None) else str(local)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        res = step()
+        ends[i].record(stream)
+        kernel_ms.append(gcpkg.last_phase_ms()[2])
+        launches += gcpkg.last_launch_count()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(tt.item())
+    value = world * args.steps * g.m / total_s
+
+    sizes, vols = gcpkg.last_round_stats()
+    elem = 2 if g.max_degree + 1 <= 65535 else 4
+    alg_bytes = algorithmic_bytes_rounds(sizes, vols, elem)
+    kms = statistics.mean(kernel_ms)
+    achieved = alg_bytes / (kms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = load_traffic(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(g.rowptr).pin_memory()
+        h_ci = torch.from_numpy(g.colidx).pin_memory()
+        h_out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            gcpkg.color_host(h_rp, h_ci, out=h_out, stream=stream)
+        torch.cuda.synchronize(dev)
+        e_ms = []
+        for _ in range(max(3, args.steps // 5)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r2 = gcpkg.color_host(h_rp, h_ci, out=h_out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        assert np.array_equal(h_out.numpy(), out.cpu().numpy()) and r2.ncolors == res.ncolors
+        e2e = {"value": g.m / (statistics.mean(e_ms) / 1e3), "unit": "edges/s",
+               "h2d_bytes_per_step": 4 * (g.n + 1) + 4 * g.nnz, "d2h_bytes_per_step": 4 * g.n + 8,
+               "ms_per_step": statistics.mean(e_ms)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cg, cr, ct = oracle_rate(CPU_BASELINE_SCALE)
+        cpu = {"value": cg.m / ct[0], "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": (f"R-MAT-B scale {CPU_BASELINE_SCALE} (same recipe, seed 3): {cg.m} edges, "
+                          f"one full run, {ct[0]:.1f} s, {cr.rounds} rounds, {cr.ncolors} colors")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "ncolors": res.ncolors, "rounds": res.rounds,
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "max_degree": g.max_degree,
+                       "priority": "index (plain)", "loop": "persistent cooperative launch",
+                       "color_state_bits": 8 * elem,
+                       "l2": "inputs larger than L2 (colidx 1.07 GB) and L2 flushed (256 MB write) "
+                             "before every step, outside its events",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "rounds_persistent_kernel",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes": alg_bytes, "kernel_ms": kms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

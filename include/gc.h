@@ -1,0 +1,169 @@
+/*
+ * gc.h - C ABI of the GB300 speculative distance-1 graph coloring library
+ * (libgc.so).
+ *
+ * Method: Algorithm 2 ("Iterative", Sec. 3.2) of Catalyurek, Feo,
+ * Gebremedhin, Halappanavar and Pothen, "Graph coloring algorithms for
+ * multi-core and massively multithreaded architectures" (arXiv 1205.3809),
+ * run in synchronous rounds over a worklist U (initially all vertices):
+ *   Phase 1 (tentative coloring): every v in U takes the smallest color > 0
+ *     that none of its neighbours held at the end of the previous round
+ *     (first fit, Algorithm 1 / Sec. 3.1);
+ *   Phase 2 (conflict detection): v in U goes back to U if a neighbour w
+ *     with the same color precedes it, where w precedes v iff
+ *     (priority[w], w) < (priority[v], v); with no priority array this is the
+ *     paper's rule that the higher index recolors;
+ * until U is empty.  Because each round reads only the previous round's
+ * colors, the result is a pure function of the graph and the priority.
+ *
+ * Conventions for every entry point:
+ *  - Graph: simple undirected graph as a symmetric CSR of int32: rowptr has
+ *    n+1 entries, rowptr[0] = 0, non-decreasing, nnz = rowptr[n] < 2^31;
+ *    colidx has nnz entries, each in [0, n); adjacency must be symmetric (a
+ *    one-directional entry could hide a conflict) and free of self loops.
+ *    Rows need not be sorted.  Duplicate entries are harmless.
+ *  - Device pointers are global-memory pointers of the current CUDA device;
+ *    the caller owns them; inputs are never modified.
+ *  - Colors are written as int32 in 1..ncolors.
+ *  - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) and return after the host outputs are known, i.e. they
+ *    synchronise that stream once at the end (and once after the setup scan).
+ *  - Errors are returned as a gc_status code; nothing is thrown or aborted.
+ *    After GC_ERR_CUDA the CUDA error is available from gc_last_cuda_error().
+ *  - The library keeps a per-device workspace (grow only) between calls;
+ *    gc_release() frees it.  Calls from several host threads are serialised.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gc_status {
+    GC_OK = 0,
+    GC_ERR_INVALID = -1,    /* bad argument (null pointer, n < 0, bad option) */
+    GC_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    GC_ERR_OOM = -3,        /* workspace allocation failed */
+    GC_ERR_MAX_ROUNDS = -4, /* U not empty after max_rounds rounds */
+    GC_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+    GC_ERR_BAD_GRAPH = -6   /* CSR rejected by the setup scan or validation */
+} gc_status;
+
+/*
+ * Options.  Zero-initialise and set what you need; 0 selects the default.
+ */
+typedef struct gc_options {
+    int32_t thread_max_degree; /* vertices with degree <= this are colored
+                                  thread-per-vertex (1..63, default 24) */
+    int32_t warp_max_degree;   /* degree <= this (and above the previous bin)
+                                  warp-per-vertex; above it block-per-vertex
+                                  (default 2048) */
+    int32_t max_rounds;        /* stop with GC_ERR_MAX_ROUNDS after this many
+                                  rounds (default n; rounds <= n always holds,
+                                  since the first vertex of U in precedence
+                                  order settles in every round) */
+    int32_t validate;          /* 1: check colidx range, self loops and
+                                  symmetry on the device before coloring */
+    int32_t loop_mode;         /* 0: all rounds in one persistent cooperative
+                                  launch (default); 1: one launch per round,
+                                  the host reads |U| after each */
+    int32_t color_bits;        /* 0: automatic (16-bit color state when the
+                                  maximum degree is below 65535, else 32);
+                                  16 or 32 to force one */
+    int32_t block_threads;     /* threads per block: 128, 256 (default) or 512 */
+    int32_t telemetry;         /* 1: time the phases with CUDA events on the
+                                  call's stream (see gc_last_phase_ms) */
+    int32_t reserved[8];
+} gc_options;
+
+/*
+ * gc_color - color the graph (Algorithm 2, synchronous rounds).
+ *   rowptr, colidx : device, CSR as above.
+ *   n              : vertex count (>= 0).
+ *   priority       : device, n uint32 keys, or NULL for index priority.
+ *                    Smaller key = higher precedence; ties go by index.
+ *   colors_out     : device, n int32 (caller-allocated), receives 1-based colors.
+ *   ncolors        : host, receives the largest color (0 when n == 0).
+ *   rounds         : host, receives the number of rounds (0 iff n == 0).
+ * Returns GC_OK or a gc_status code.  On an error colors_out is unspecified.
+ */
+int gc_color(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+             int32_t* colors_out, int32_t* ncolors, int32_t* rounds);
+
+/*
+ * gc_color_ex - gc_color with a stream, options and per-round telemetry.
+ *   stream          : cudaStream_t to run on (NULL = default stream).
+ *   opt             : options or NULL for defaults.
+ *   round_sizes     : host, optional (NULL): round_sizes[r-1] = |U| at the
+ *                     start of round r, for r = 1..min(rounds, round_sizes_cap,
+ *                     2^20).
+ */
+int gc_color_ex(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                int32_t* colors_out, int32_t* ncolors, int32_t* rounds, void* stream,
+                const gc_options* opt, int32_t* round_sizes, int32_t round_sizes_cap);
+
+/*
+ * gc_color_host - the same computation on a graph held in HOST memory.
+ *   rowptr, colidx, priority (or NULL): host arrays, as above.
+ *   colors_out : host, n int32.
+ * The library copies the inputs into its device workspace on `stream`,
+ * colors, and copies the colors back; pinned host buffers copy fastest.
+ */
+int gc_color_host(const int32_t* rowptr, const int32_t* colidx, int32_t n,
+                  const uint32_t* priority, int32_t* colors_out, int32_t* ncolors,
+                  int32_t* rounds, void* stream, const gc_options* opt);
+
+/*
+ * gc_validate_csr - device check of a CSR graph (rowptr shape, colidx range,
+ * no self loops, symmetric adjacency).  Symmetry is tested by comparing two
+ * 64-bit hash sums of the entry multiset and of its transpose, so an
+ * asymmetric graph passes with probability about 2^-64.
+ * Returns GC_OK, GC_ERR_BAD_GRAPH, or another gc_status code.
+ */
+int gc_validate_csr(const int32_t* rowptr, const int32_t* colidx, int32_t n, void* stream);
+
+/*
+ * gc_last_round_stats - per-round telemetry of the last successful coloring
+ * call on the current device: sizes[r-1] = |U_r| and volumes[r-1] = the sum of
+ * the degrees of the vertices of U_r (the adjacency entries round r's Phase 1
+ * reads), for r = 1..min(rounds, cap, 4096 or the round_sizes_cap of that
+ * call).  Either output may be NULL.  Returns the number of rounds written,
+ * or a negative gc_status (GC_ERR_INVALID if there is no such call).
+ */
+int gc_last_round_stats(int32_t* sizes, int64_t* volumes, int32_t cap);
+
+/*
+ * gc_last_phase_ms - phase timings, in milliseconds from CUDA events recorded
+ * on the call's stream, of the last call made with opt->telemetry = 1:
+ * ms[0] setup scan kernel, ms[1] round 1 (the two pass-1 kernels), ms[2]
+ * every later round (the persistent kernel, or all per-round launches with
+ * their host round trips in loop_mode 1), ms[3] the whole call.
+ * Returns the number of values written (<= cap, at most 4) or GC_ERR_INVALID.
+ */
+int gc_last_phase_ms(float* ms, int32_t cap);
+
+/* Text for a gc_status code (static storage). */
+const char* gc_strerror(int code);
+
+/* The CUDA error code (cudaError_t) behind the last GC_ERR_CUDA, or 0. */
+int gc_last_cuda_error(void);
+
+/* Free the workspace of every device this process used.  Returns GC_OK. */
+int gc_release(void);
+
+/* Bytes of device workspace currently held on the current device. */
+size_t gc_workspace_bytes(void);
+
+/* Number of kernel launches made by the last successful call on this
+ * process (for launch accounting). */
+int64_t gc_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

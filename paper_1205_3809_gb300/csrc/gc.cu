@@ -1,0 +1,540 @@
+// Host driver and C ABI of libgc.so (declarations and contracts in gc.h).
+//
+// One call of gc_color_ex:
+//   1. stats_kernel scans rowptr: max degree, vertices per degree bin, shape
+//      checks; one device-to-host copy decides the color width (16-bit color
+//      state when every first-fit color fits, i.e. max degree + 1 <= 65535)
+//      and sizes the workspace;
+//   2. pass1_thread_kernel + pass1_big_kernel: round 1 (closed form, all
+//      colors 1), its conflict test, and round 2's colors (all 2);
+//   3. rounds_persistent_kernel: every later round in one cooperative launch
+//      (or, with loop_mode = 1, one round_kernel launch per round);
+//   4. one device-to-host copy of the round state and telemetry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "gc.h"
+#include "gc_device.cuh"
+
+namespace {
+
+using gc::Params;
+using gc::RoundState;
+using gc::Stats;
+
+std::mutex g_mu;
+int g_last_cuda_error = 0;
+int64_t g_last_launches = 0;
+
+// Record of the last successful coloring call (for the telemetry queries).
+struct LastCall {
+    int valid = 0;
+    int device = -1;
+    int32_t rounds = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t cap = 0;
+    const int32_t* d_sizes = nullptr;          // device, workspace
+    const unsigned long long* d_vol = nullptr; // device, workspace
+    int timed = 0;
+    float ms[4] = {0, 0, 0, 0};
+};
+LastCall g_last;
+
+struct DeviceCache {
+    void* ws = nullptr;        // coloring workspace
+    size_t ws_bytes = 0;
+    void* in = nullptr;        // device copies of host inputs (gc_color_host)
+    size_t in_bytes = 0;
+    void* host = nullptr;      // pinned host staging for results
+    size_t host_bytes = 0;
+    int sms = 0;
+    int coop = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+std::map<int, DeviceCache> g_cache;
+
+#define GC_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            g_last_cuda_error = (int)e_;                    \
+            (void)cudaGetLastError();                       \
+            return e_ == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA; \
+        }                                                   \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int device_cache(DeviceCache** out) {
+    int dev = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    DeviceCache& c = g_cache[dev];
+    if (c.sms == 0) {
+        GC_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+        GC_CUDA(cudaDeviceGetAttribute(&c.coop, cudaDevAttrCooperativeLaunch, dev));
+    }
+    *out = &c;
+    return GC_OK;
+}
+
+int ensure_device(void** p, size_t* have, size_t need) {
+    if (*have >= need && *p) return GC_OK;
+    if (*p) {
+        GC_CUDA(cudaDeviceSynchronize());
+        GC_CUDA(cudaFree(*p));
+        *p = nullptr;
+        *have = 0;
+    }
+    GC_CUDA(cudaMalloc(p, need));
+    *have = need;
+    return GC_OK;
+}
+
+int ensure_host(void** p, size_t* have, size_t need) {
+    if (*have >= need && *p) return GC_OK;
+    if (*p) {
+        GC_CUDA(cudaFreeHost(*p));
+        *p = nullptr;
+        *have = 0;
+    }
+    GC_CUDA(cudaMallocHost(p, need));
+    *have = need;
+    return GC_OK;
+}
+
+struct Layout {
+    size_t st, stats, rs, rv, x0, x1, l[6], total;
+};
+
+Layout make_layout(int64_t n, size_t elem, const unsigned bins[3], int64_t round_cap) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L.st = take(sizeof(RoundState));
+    L.stats = take(sizeof(Stats));
+    L.rs = take((size_t)round_cap * sizeof(int32_t));
+    L.rv = take((size_t)round_cap * sizeof(unsigned long long));
+    L.x0 = take((size_t)n * elem);
+    L.x1 = take((size_t)n * elem);
+    for (int buf = 0; buf < 2; ++buf)
+        for (int b = 0; b < 3; ++b) L.l[buf * 3 + b] = take((size_t)std::max(bins[b], 1u) * sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
+    const int threads = o.block_threads;
+    {
+        const int64_t want = (p.n + 255) / 256;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)dc.sms * 8));
+        gc::pass1_thread_kernel<T><<<grid, 256, 0, s>>>(p);
+        GC_CUDA(cudaGetLastError());
+        gc::pass1_big_kernel<T><<<dc.sms * 4, 256, 0, s>>>(p);
+        GC_CUDA(cudaGetLastError());
+        *launches += 2;
+        if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
+    }
+    if (o.loop_mode == 0) {
+        int per_sm = 0;
+        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, gc::rounds_persistent_kernel<T>, threads, 0));
+        if (per_sm < 1 || !dc.coop) return GC_ERR_CUDA;
+        dim3 grid(per_sm * dc.sms), block(threads);
+        void* args[] = {&p};
+        GC_CUDA(cudaLaunchCooperativeKernel((const void*)gc::rounds_persistent_kernel<T>, grid, block,
+                                            args, 0, s));
+        *launches += 1;
+        return GC_OK;
+    }
+    // loop_mode 1: the host reads |U_k| after each pass
+    unsigned* h = nullptr;
+    size_t have = dc.host_bytes;
+    int rc = ensure_host(&dc.host, &have, 4096);
+    if (rc != GC_OK) return rc;
+    dc.host_bytes = have;
+    // pinned slots: h[0..2] counts read back, h[4] size, h[5] status, h[6] rounds; every
+    // iteration synchronises the stream before a slot is rewritten
+    h = (unsigned*)dc.host;
+    int32_t* hs = (int32_t*)(h + 4);
+    RoundState* st = p.st;
+    int k = 2;
+    for (;; ++k) {
+        GC_CUDA(cudaMemcpyAsync(h, st->cnt[k % 3], 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        const unsigned nL = h[0], nM = h[1], nH = h[2];
+        const unsigned size = nL + nM + nH;
+        if (size == 0) break;
+        if (k > p.max_rounds) {
+            hs[1] = gc::kStatusMaxRounds;
+            GC_CUDA(cudaMemcpyAsync(&st->status, &hs[1], sizeof(int), cudaMemcpyHostToDevice, s));
+            break;
+        }
+        if (k - 1 < p.round_cap) {
+            hs[0] = (int32_t)size;
+            GC_CUDA(cudaMemcpyAsync(p.round_sizes + (k - 1), &hs[0], sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        }
+        GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 3 * sizeof(unsigned), s));
+        GC_CUDA(cudaMemsetAsync(&st->tick[(k + 2) % 3], 0, sizeof(unsigned), s));
+        const unsigned warps = threads / 32;
+        const int64_t tasks = (int64_t)nH + (nM + warps - 1) / warps + (nL + threads - 1) / threads;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)dc.sms * 4));
+        gc::round_kernel<T><<<grid, threads, 0, s>>>(p, k, nL, nM, nH);
+        GC_CUDA(cudaGetLastError());
+        *launches += 1;
+    }
+    hs[2] = k - 1;
+    GC_CUDA(cudaMemcpyAsync(&st->rounds, &hs[2], sizeof(int), cudaMemcpyHostToDevice, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    return GC_OK;
+}
+
+int normalise(const gc_options* opt, gc_options* o) {
+    std::memset(o, 0, sizeof(*o));
+    if (opt) *o = *opt;
+    if (o->thread_max_degree == 0) o->thread_max_degree = 24;
+    if (o->warp_max_degree == 0) o->warp_max_degree = 2048;
+    if (o->block_threads == 0) o->block_threads = 256;
+    if (o->thread_max_degree < 1 || o->thread_max_degree > 63) return GC_ERR_INVALID;
+    if (o->warp_max_degree < o->thread_max_degree) return GC_ERR_INVALID;
+    if (o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512) return GC_ERR_INVALID;
+    if (o->loop_mode != 0 && o->loop_mode != 1) return GC_ERR_INVALID;
+    if (o->color_bits != 0 && o->color_bits != 16 && o->color_bits != 32) return GC_ERR_INVALID;
+    if (o->max_rounds < 0 || o->validate < 0 || o->validate > 1) return GC_ERR_INVALID;
+    if (o->telemetry != 0 && o->telemetry != 1) return GC_ERR_INVALID;
+    return GC_OK;
+}
+
+int validate_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, cudaStream_t s,
+                    DeviceCache& dc, int64_t* launches) {
+    // workspace head is reused for the validation record
+    int rc = ensure_device(&dc.ws, &dc.ws_bytes, std::max<size_t>(dc.ws_bytes, 4096));
+    if (rc != GC_OK) return rc;
+    gc::ValidateOut* out = (gc::ValidateOut*)dc.ws;
+    Stats* stats = (Stats*)((char*)dc.ws + 1024);
+    GC_CUDA(cudaMemsetAsync(dc.ws, 0, 2048, s));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)dc.sms * 8));
+    gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, 63, 63, stats);
+    GC_CUDA(cudaGetLastError());
+    size_t hb = dc.host_bytes;
+    rc = ensure_host(&dc.host, &hb, 4096);
+    if (rc != GC_OK) return rc;
+    dc.host_bytes = hb;
+    GC_CUDA(cudaMemcpyAsync(dc.host, stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    Stats hs;
+    std::memcpy(&hs, dc.host, sizeof(Stats));
+    *launches += 1;
+    if (hs.bad || hs.nnz < 0) return GC_ERR_BAD_GRAPH;
+    if (hs.nnz > 0 && !colidx) return GC_ERR_INVALID;
+    const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n * 32 + 255) / 256, (int64_t)dc.sms * 16));
+    gc::validate_kernel<<<vgrid, 256, 0, s>>>(rowptr, colidx, n, out);
+    GC_CUDA(cudaGetLastError());
+    *launches += 1;
+    GC_CUDA(cudaMemcpyAsync(dc.host, out, sizeof(gc::ValidateOut), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    gc::ValidateOut ho;
+    std::memcpy(&ho, dc.host, sizeof(ho));
+    if (ho.bad_index || ho.self_loop || ho.sum_fwd != ho.sum_bwd) return GC_ERR_BAD_GRAPH;
+    return GC_OK;
+}
+
+int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                 int32_t* colors_out, int32_t* ncolors, int32_t* rounds, cudaStream_t s,
+                 const gc_options* opt, int32_t* round_sizes, int32_t round_sizes_cap) {
+    gc_options o;
+    int rc = normalise(opt, &o);
+    if (rc != GC_OK) return rc;
+    if (n < 0 || !ncolors || !rounds || (round_sizes && round_sizes_cap < 0)) return GC_ERR_INVALID;
+    g_last.valid = 0;
+    if (n > 0 && (!rowptr || !colors_out)) return GC_ERR_INVALID;
+    int64_t launches = 0;
+    if (n == 0) {
+        *ncolors = 0;
+        *rounds = 0;
+        g_last_launches = 0;
+        return GC_OK;
+    }
+    DeviceCache* dcp = nullptr;
+    rc = device_cache(&dcp);
+    if (rc != GC_OK) return rc;
+    DeviceCache& dc = *dcp;
+    if (o.validate) {
+        rc = validate_locked(rowptr, colidx, n, s, dc, &launches);
+        if (rc != GC_OK) return rc;
+    }
+    const int32_t max_rounds = o.max_rounds > 0 ? o.max_rounds : n;
+    // telemetry covers the first min(rounds, max(4096, caller cap), 2^20) rounds
+    const int64_t round_cap = std::max<int64_t>(1, std::min<int64_t>(
+        max_rounds, std::max<int64_t>(4096, std::min<int64_t>(round_sizes ? round_sizes_cap : 0, 1 << 20))));
+
+    // 1. setup scan (its record lives in a small fixed head of the workspace)
+    rc = ensure_device(&dc.ws, &dc.ws_bytes, std::max<size_t>(dc.ws_bytes, 4096));
+    if (rc != GC_OK) return rc;
+    size_t hb = dc.host_bytes;
+    rc = ensure_host(&dc.host, &hb, std::max<size_t>(4096, sizeof(RoundState) + (size_t)round_cap * 4));
+    if (rc != GC_OK) return rc;
+    dc.host_bytes = hb;
+    if (o.telemetry && !dc.ev[0])
+        for (int i = 0; i < 4; ++i) GC_CUDA(cudaEventCreate(&dc.ev[i]));
+    if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[0], s));
+    {
+        Stats* stats = (Stats*)dc.ws;
+        GC_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), s));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)dc.sms * 8));
+        gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, o.thread_max_degree, o.warp_max_degree, stats);
+        GC_CUDA(cudaGetLastError());
+        launches += 1;
+        if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[1], s));
+        GC_CUDA(cudaMemcpyAsync(dc.host, stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    }
+    Stats hs;
+    std::memcpy(&hs, dc.host, sizeof(Stats));
+    if (hs.bad || hs.nnz < 0) return GC_ERR_BAD_GRAPH;
+    if (hs.nnz > 0 && !colidx) return GC_ERR_INVALID;
+    int bits = o.color_bits;
+    if (bits == 0) bits = (hs.max_degree + 1 <= 65535) ? 16 : 32;
+    if (bits == 16 && hs.max_degree + 1 > 65535) return GC_ERR_INVALID;
+    const size_t elem = bits == 16 ? 2 : 4;
+
+    // 2. workspace
+    const Layout L = make_layout(n, elem, hs.bin_count, round_cap);
+    rc = ensure_device(&dc.ws, &dc.ws_bytes, L.total);
+    if (rc != GC_OK) return rc;
+    char* base = (char*)dc.ws;
+    RoundState* st = (RoundState*)(base + L.st);
+    GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
+    GC_CUDA(cudaMemsetAsync(base + L.rv, 0, (size_t)round_cap * sizeof(unsigned long long), s));
+
+    auto fill = [&](auto& p) {
+        using PT = std::remove_reference_t<decltype(p)>;
+        using T = std::remove_pointer_t<decltype(PT::X0)>;
+        p.rowptr = rowptr;
+        p.colidx = colidx;
+        p.prio = priority;
+        p.n = n;
+        p.t1 = o.thread_max_degree;
+        p.t2 = o.warp_max_degree;
+        p.max_rounds = max_rounds;
+        p.X0 = (T*)(base + L.x0);
+        p.X1 = (T*)(base + L.x1);
+        p.colors_out = colors_out;
+        p.listA0 = (int32_t*)(base + L.l[0]);
+        p.listA1 = (int32_t*)(base + L.l[1]);
+        p.listA2 = (int32_t*)(base + L.l[2]);
+        p.listB0 = (int32_t*)(base + L.l[3]);
+        p.listB1 = (int32_t*)(base + L.l[4]);
+        p.listB2 = (int32_t*)(base + L.l[5]);
+        p.st = st;
+        p.round_sizes = (int32_t*)(base + L.rs);
+        p.round_vol = (unsigned long long*)(base + L.rv);
+        p.round_cap = (int32_t)round_cap;
+    };
+    if (bits == 16) {
+        Params<uint16_t> p;
+        fill(p);
+        rc = run_rounds(o, dc, p, s, &launches);
+    } else {
+        Params<int32_t> p;
+        fill(p);
+        rc = run_rounds(o, dc, p, s, &launches);
+    }
+    if (rc != GC_OK) return rc;
+
+    // 4. results
+    if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[3], s));
+    GC_CUDA(cudaMemcpyAsync(dc.host, st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    RoundState hst;
+    std::memcpy(&hst, dc.host, sizeof(RoundState));
+    if (hst.status == gc::kStatusTimeout) return GC_ERR_TIMEOUT;
+    g_last.valid = 1;
+    GC_CUDA(cudaGetDevice(&g_last.device));
+    g_last.rounds = hst.rounds;
+    g_last.n = n;
+    g_last.nnz = hs.nnz;
+    g_last.cap = (int32_t)round_cap;
+    g_last.d_sizes = (const int32_t*)(base + L.rs);
+    g_last.d_vol = (const unsigned long long*)(base + L.rv);
+    g_last.timed = o.telemetry;
+    if (o.telemetry) {
+        GC_CUDA(cudaEventElapsedTime(&g_last.ms[0], dc.ev[0], dc.ev[1]));
+        GC_CUDA(cudaEventElapsedTime(&g_last.ms[1], dc.ev[1], dc.ev[2]));
+        GC_CUDA(cudaEventElapsedTime(&g_last.ms[2], dc.ev[2], dc.ev[3]));
+        GC_CUDA(cudaEventElapsedTime(&g_last.ms[3], dc.ev[0], dc.ev[3]));
+    }
+    *rounds = hst.rounds;
+    *ncolors = hst.max_color;
+    if (round_sizes && round_sizes_cap > 0) {
+        const int64_t m = std::min<int64_t>({(int64_t)hst.rounds, (int64_t)round_sizes_cap, round_cap});
+        round_sizes[0] = n;
+        if (m > 1) {
+            GC_CUDA(cudaMemcpyAsync(dc.host, base + L.rs + sizeof(int32_t), (size_t)(m - 1) * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s));
+            GC_CUDA(cudaStreamSynchronize(s));
+            std::memcpy(round_sizes + 1, dc.host, (size_t)(m - 1) * sizeof(int32_t));
+        }
+    }
+    g_last_launches = launches;
+    if (hst.status == gc::kStatusMaxRounds) return GC_ERR_MAX_ROUNDS;
+    return GC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gc_color_ex(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                int32_t* colors_out, int32_t* ncolors, int32_t* rounds, void* stream,
+                const gc_options* opt, int32_t* round_sizes, int32_t round_sizes_cap) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_last_cuda_error = 0;
+    return color_locked(rowptr, colidx, n, priority, colors_out, ncolors, rounds, (cudaStream_t)stream,
+                        opt, round_sizes, round_sizes_cap);
+}
+
+int gc_color(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+             int32_t* colors_out, int32_t* ncolors, int32_t* rounds) {
+    return gc_color_ex(rowptr, colidx, n, priority, colors_out, ncolors, rounds, nullptr, nullptr,
+                       nullptr, 0);
+}
+
+int gc_color_host(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                  int32_t* colors_out, int32_t* ncolors, int32_t* rounds, void* stream,
+                  const gc_options* opt) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_last_cuda_error = 0;
+    if (n < 0 || !ncolors || !rounds) return GC_ERR_INVALID;
+    if (n == 0) {
+        *ncolors = 0;
+        *rounds = 0;
+        return GC_OK;
+    }
+    if (!rowptr || !colors_out) return GC_ERR_INVALID;
+    const int64_t nnz = rowptr[n];
+    if (rowptr[0] != 0 || nnz < 0) return GC_ERR_BAD_GRAPH;
+    if (nnz > 0 && !colidx) return GC_ERR_INVALID;
+    DeviceCache* dcp = nullptr;
+    int rc = device_cache(&dcp);
+    if (rc != GC_OK) return rc;
+    DeviceCache& dc = *dcp;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b_rp = align_up((size_t)(n + 1) * 4, 256), b_ci = align_up((size_t)nnz * 4 + 4, 256),
+                 b_pr = priority ? align_up((size_t)n * 4, 256) : 0, b_co = align_up((size_t)n * 4, 256);
+    rc = ensure_device(&dc.in, &dc.in_bytes, b_rp + b_ci + b_pr + b_co);
+    if (rc != GC_OK) return rc;
+    char* base = (char*)dc.in;
+    int32_t* d_rp = (int32_t*)base;
+    int32_t* d_ci = (int32_t*)(base + b_rp);
+    uint32_t* d_pr = priority ? (uint32_t*)(base + b_rp + b_ci) : nullptr;
+    int32_t* d_co = (int32_t*)(base + b_rp + b_ci + b_pr);
+    GC_CUDA(cudaMemcpyAsync(d_rp, rowptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) GC_CUDA(cudaMemcpyAsync(d_ci, colidx, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    if (priority) GC_CUDA(cudaMemcpyAsync(d_pr, priority, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    rc = color_locked(d_rp, d_ci, n, d_pr, d_co, ncolors, rounds, s, opt, nullptr, 0);
+    if (rc != GC_OK) return rc;
+    GC_CUDA(cudaMemcpyAsync(colors_out, d_co, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    return GC_OK;
+}
+
+int gc_validate_csr(const int32_t* rowptr, const int32_t* colidx, int32_t n, void* stream) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_last_cuda_error = 0;
+    if (n < 0 || (n > 0 && !rowptr)) return GC_ERR_INVALID;
+    if (n == 0) return GC_OK;
+    DeviceCache* dcp = nullptr;
+    int rc = device_cache(&dcp);
+    if (rc != GC_OK) return rc;
+    int64_t launches = 0;
+    rc = validate_locked(rowptr, colidx, n, (cudaStream_t)stream, *dcp, &launches);
+    g_last_launches = launches;
+    return rc;
+}
+
+const char* gc_strerror(int code) {
+    switch (code) {
+        case GC_OK: return "ok";
+        case GC_ERR_INVALID: return "invalid argument";
+        case GC_ERR_CUDA: return "CUDA runtime error";
+        case GC_ERR_OOM: return "out of device memory";
+        case GC_ERR_MAX_ROUNDS: return "worklist not empty after max_rounds rounds";
+        case GC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case GC_ERR_BAD_GRAPH: return "graph rejected (CSR shape, index range, self loop or asymmetry)";
+        default: return "unknown gc_status";
+    }
+}
+
+int gc_last_cuda_error(void) { return g_last_cuda_error; }
+
+int gc_last_round_stats(int32_t* sizes, int64_t* volumes, int32_t cap) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_last.valid || cap < 0) return GC_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g_last.device) return GC_ERR_INVALID;
+    const int32_t m = std::min({g_last.rounds, cap, g_last.cap});
+    if (m <= 0) return 0;
+    if (sizes) {
+        sizes[0] = g_last.n;
+        if (m > 1) GC_CUDA(cudaMemcpy(sizes + 1, g_last.d_sizes + 1, (size_t)(m - 1) * 4, cudaMemcpyDeviceToHost));
+    }
+    if (volumes) {
+        volumes[0] = g_last.nnz;
+        if (m > 1) GC_CUDA(cudaMemcpy(volumes + 1, g_last.d_vol + 1, (size_t)(m - 1) * 8, cudaMemcpyDeviceToHost));
+    }
+    return m;
+}
+
+int gc_last_phase_ms(float* ms, int32_t cap) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_last.valid || !g_last.timed || !ms || cap < 0) return GC_ERR_INVALID;
+    const int m = std::min(cap, 4);
+    for (int i = 0; i < m; ++i) ms[i] = g_last.ms[i];
+    return m;
+}
+
+int gc_release(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : g_cache) {
+        cudaSetDevice(kv.first);
+        cudaDeviceSynchronize();
+        if (kv.second.ws) cudaFree(kv.second.ws);
+        if (kv.second.in) cudaFree(kv.second.in);
+        if (kv.second.host) cudaFreeHost(kv.second.host);
+        for (int i = 0; i < 4; ++i)
+            if (kv.second.ev[i]) cudaEventDestroy(kv.second.ev[i]);
+    }
+    g_cache.clear();
+    g_last.valid = 0;
+    cudaSetDevice(cur);
+    (void)cudaGetLastError();
+    return GC_OK;
+}
+
+size_t gc_workspace_bytes(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    auto it = g_cache.find(dev);
+    return it == g_cache.end() ? 0 : it->second.ws_bytes + it->second.in_bytes;
+}
+
+int64_t gc_last_launch_count(void) { return g_last_launches; }
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+"""Write tests/golden/fullsize.json: the oracle's result on the full-size
+synthetic workloads, stored as a SHA-256 of the int32 colors plus ncolors,
+rounds and |U_r| of every round.  Calls only graphgen/ and oracle/.
+
+    python tests/golden/make_fullsize.py [name ...]
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+import oracle  # noqa: E402
+
+WORKLOADS = {
+    # R-MAT-B scale 24 (16,777,216 vertices, edge factor 8), (0.55,0.15,0.15,0.15), seed 3
+    "rmat_b_s24_seed3": lambda: gg.rmat(24, 8, gg.RMAT_B, 3),
+    # R-MAT-G scale 23 (8,388,608 vertices, edge factor 8), (0.45,0.15,0.15,0.25), seed 5
+    "rmat_g_s23_seed5": lambda: gg.rmat(23, 8, gg.RMAT_G, 5),
+}
+
+
+def sha(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).astype("<i4").tobytes()).hexdigest()
+
+
+def main(names):
+    path = os.path.join(ROOT, "tests", "golden", "fullsize.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    for name in names:
+        g = WORKLOADS[name]()
+        t = time.time()
+        r = oracle.iterative(g.rowptr, g.colidx)
+        out[name] = {
+            "n": g.n, "nnz": g.nnz,
+            "graph_sha256": hashlib.sha256(g.rowptr.astype("<i4").tobytes()
+                                           + g.colidx.astype("<i4").tobytes()).hexdigest(),
+            "colors_sha256": sha(r.colors), "ncolors": r.ncolors, "rounds": r.rounds,
+            "round_sizes": r.round_sizes.tolist(),
+            "oracle_seconds": round(time.time() - t, 1),
+        }
+        print(name, out[name]["ncolors"], out[name]["rounds"], out[name]["oracle_seconds"], flush=True)
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+            f.write("\n")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(WORKLOADS))
