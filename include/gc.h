@@ -57,11 +57,12 @@ typedef enum gc_status {
  * Options.  Zero-initialise and set what you need; 0 selects the default.
  */
 typedef struct gc_options {
-    int32_t thread_max_degree; /* vertices with degree <= this are colored
-                                  thread-per-vertex (1..63, default 24) */
-    int32_t warp_max_degree;   /* degree <= this (and above the previous bin)
-                                  warp-per-vertex; above it block-per-vertex
-                                  (default 2048) */
+    int32_t small_max_degree;  /* vertices of degree <= this are processed by
+                                  4 lanes each, 8 per warp (1..32, default 32) */
+    int32_t medium_max_degree; /* degree <= this (and above the small bin):
+                                  one warp per vertex; above it the adjacency
+                                  is split into 256-entry chunks, one warp
+                                  each (small_max_degree..256, default 256) */
     int32_t max_rounds;        /* stop with GC_ERR_MAX_ROUNDS after this many
                                   rounds (default n; rounds <= n always holds,
                                   since the first vertex of U in precedence
@@ -74,7 +75,7 @@ typedef struct gc_options {
     int32_t color_bits;        /* 0: automatic (16-bit color state when the
                                   maximum degree is below 65535, else 32);
                                   16 or 32 to force one */
-    int32_t block_threads;     /* threads per block: 128, 256 (default) or 512 */
+    int32_t block_threads;     /* threads per block: 128 or 256 (default) */
     int32_t telemetry;         /* 1: time the phases with CUDA events on the
                                   call's stream (see gc_last_phase_ms) */
     int32_t reserved[8];

@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 class Options(ctypes.Structure):
     """Mirror of ``gc_options`` (gc.h).  0 selects each default."""
-    _fields_ = [("thread_max_degree", ctypes.c_int32), ("warp_max_degree", ctypes.c_int32),
+    _fields_ = [("small_max_degree", ctypes.c_int32), ("medium_max_degree", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("color_bits", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),

@@ -111,15 +111,17 @@ int ensure_host(void** p, size_t* have, size_t need) {
 }
 
 struct Layout {
-    size_t st, stats, rs, rv, x0, x1, l[6], total;
+    size_t st, stats, rs, rv, x0, x1, hubs, defer;
+    size_t S[2], M[2], H[2], Hc[2], O[2];
+    size_t total;
 };
 
-Layout make_layout(int64_t n, size_t elem, const unsigned bins[3], int64_t round_cap) {
+Layout make_layout(int64_t n, size_t elem, const Stats& hs, int64_t round_cap) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
-        off = align_up(off + bytes, 256);
+        off = align_up(off + std::max<size_t>(bytes, 4), 256);
         return o;
     };
     L.st = take(sizeof(RoundState));
@@ -128,8 +130,15 @@ Layout make_layout(int64_t n, size_t elem, const unsigned bins[3], int64_t round
     L.rv = take((size_t)round_cap * sizeof(unsigned long long));
     L.x0 = take((size_t)n * elem);
     L.x1 = take((size_t)n * elem);
-    for (int buf = 0; buf < 2; ++buf)
-        for (int b = 0; b < 3; ++b) L.l[buf * 3 + b] = take((size_t)std::max(bins[b], 1u) * sizeof(int32_t));
+    L.hubs = take((size_t)hs.bin_count[gc::kBinH] * sizeof(gc::HubRecord));
+    L.defer = take((size_t)hs.defer * sizeof(int32_t));
+    for (int b = 0; b < 2; ++b) {
+        L.S[b] = take((size_t)hs.bin_count[gc::kBinS] * sizeof(int32_t));
+        L.M[b] = take((size_t)hs.bin_count[gc::kBinM] * sizeof(int32_t));
+        L.H[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int32_t));
+        L.Hc[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int32_t));
+        L.O[b] = take((size_t)hs.hub_chunks * sizeof(int32_t));
+    }
     L.total = off;
     return L;
 }
@@ -138,11 +147,12 @@ template <typename T>
 int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
     const int threads = o.block_threads;
     {
-        const int64_t want = (p.n + 255) / 256;
+        // one warp task per 32 vertices
+        const int64_t want = ((int64_t)p.n + 255) / 256;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)dc.sms * 8));
-        gc::pass1_thread_kernel<T><<<grid, 256, 0, s>>>(p);
+        gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
-        gc::pass1_big_kernel<T><<<dc.sms * 4, 256, 0, s>>>(p);
+        gc::pass1_defer_kernel<T><<<dc.sms * 2, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
         *launches += 2;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
@@ -165,17 +175,17 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
     int rc = ensure_host(&dc.host, &have, 4096);
     if (rc != GC_OK) return rc;
     dc.host_bytes = have;
-    // pinned slots: h[0..2] counts read back, h[4] size, h[5] status, h[6] rounds; every
-    // iteration synchronises the stream before a slot is rewritten
+    // pinned slots: h[0..3] counts read back, hs[0] size, hs[1] status, hs[2] rounds;
+    // every iteration synchronises the stream before a slot is rewritten
     h = (unsigned*)dc.host;
-    int32_t* hs = (int32_t*)(h + 4);
+    int32_t* hs = (int32_t*)(h + 8);
     RoundState* st = p.st;
     int k = 2;
     for (;; ++k) {
-        GC_CUDA(cudaMemcpyAsync(h, st->cnt[k % 3], 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(h, st->cnt[k % 3], 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         GC_CUDA(cudaStreamSynchronize(s));
-        const unsigned nL = h[0], nM = h[1], nH = h[2];
-        const unsigned size = nL + nM + nH;
+        const unsigned nS = h[0], nM = h[1], nH = h[2], nHC = h[3];
+        const unsigned size = nS + nM + nH;
         if (size == 0) break;
         if (k > p.max_rounds) {
             hs[1] = gc::kStatusMaxRounds;
@@ -187,12 +197,12 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
             GC_CUDA(cudaMemcpyAsync(p.round_sizes + (k - 1), &hs[0], sizeof(int32_t),
                                     cudaMemcpyHostToDevice, s));
         }
-        GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 3 * sizeof(unsigned), s));
-        GC_CUDA(cudaMemsetAsync(&st->tick[(k + 2) % 3], 0, sizeof(unsigned), s));
-        const unsigned warps = threads / 32;
-        const int64_t tasks = (int64_t)nH + (nM + warps - 1) / warps + (nL + threads - 1) / threads;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)dc.sms * 4));
-        gc::round_kernel<T><<<grid, threads, 0, s>>>(p, k, nL, nM, nH);
+        GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 4 * sizeof(unsigned), s));
+        const int64_t tasks = (int64_t)nHC + nM + (nS + 7) / 8;
+        const int64_t warps_per_block = threads / 32;
+        const int grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>((tasks + warps_per_block - 1) / warps_per_block, (int64_t)dc.sms * 8));
+        gc::round_kernel<T><<<grid, threads, 0, s>>>(p, k, nS, nM, nHC);
         GC_CUDA(cudaGetLastError());
         *launches += 1;
     }
@@ -205,12 +215,13 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
 int normalise(const gc_options* opt, gc_options* o) {
     std::memset(o, 0, sizeof(*o));
     if (opt) *o = *opt;
-    if (o->thread_max_degree == 0) o->thread_max_degree = 24;
-    if (o->warp_max_degree == 0) o->warp_max_degree = 2048;
+    if (o->small_max_degree == 0) o->small_max_degree = gc::kSmallMaxLimit;
+    if (o->medium_max_degree == 0) o->medium_max_degree = gc::kMedMaxLimit;
     if (o->block_threads == 0) o->block_threads = 256;
-    if (o->thread_max_degree < 1 || o->thread_max_degree > 63) return GC_ERR_INVALID;
-    if (o->warp_max_degree < o->thread_max_degree) return GC_ERR_INVALID;
-    if (o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512) return GC_ERR_INVALID;
+    if (o->small_max_degree < 1 || o->small_max_degree > gc::kSmallMaxLimit) return GC_ERR_INVALID;
+    if (o->medium_max_degree < o->small_max_degree || o->medium_max_degree > gc::kMedMaxLimit)
+        return GC_ERR_INVALID;
+    if (o->block_threads != 128 && o->block_threads != 256) return GC_ERR_INVALID;
     if (o->loop_mode != 0 && o->loop_mode != 1) return GC_ERR_INVALID;
     if (o->color_bits != 0 && o->color_bits != 16 && o->color_bits != 32) return GC_ERR_INVALID;
     if (o->max_rounds < 0 || o->validate < 0 || o->validate > 1) return GC_ERR_INVALID;
@@ -227,7 +238,7 @@ int validate_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, cud
     Stats* stats = (Stats*)((char*)dc.ws + 1024);
     GC_CUDA(cudaMemsetAsync(dc.ws, 0, 2048, s));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)dc.sms * 8));
-    gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, 63, 63, stats);
+    gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, gc::kSmallMaxLimit, gc::kMedMaxLimit, stats);
     GC_CUDA(cudaGetLastError());
     size_t hb = dc.host_bytes;
     rc = ensure_host(&dc.host, &hb, 4096);
@@ -295,7 +306,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
         Stats* stats = (Stats*)dc.ws;
         GC_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), s));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)dc.sms * 8));
-        gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, o.thread_max_degree, o.warp_max_degree, stats);
+        gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, o.small_max_degree, o.medium_max_degree, stats);
         GC_CUDA(cudaGetLastError());
         launches += 1;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[1], s));
@@ -312,13 +323,14 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     const size_t elem = bits == 16 ? 2 : 4;
 
     // 2. workspace
-    const Layout L = make_layout(n, elem, hs.bin_count, round_cap);
+    const Layout L = make_layout(n, elem, hs, round_cap);
     rc = ensure_device(&dc.ws, &dc.ws_bytes, L.total);
     if (rc != GC_OK) return rc;
     char* base = (char*)dc.ws;
     RoundState* st = (RoundState*)(base + L.st);
     GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
     GC_CUDA(cudaMemsetAsync(base + L.rv, 0, (size_t)round_cap * sizeof(unsigned long long), s));
+    GC_CUDA(cudaMemsetAsync(base + L.hubs, 0, (size_t)hs.bin_count[gc::kBinH] * sizeof(gc::HubRecord), s));
 
     auto fill = [&](auto& p) {
         using PT = std::remove_reference_t<decltype(p)>;
@@ -327,18 +339,24 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
         p.colidx = colidx;
         p.prio = priority;
         p.n = n;
-        p.t1 = o.thread_max_degree;
-        p.t2 = o.warp_max_degree;
+        p.s_max = o.small_max_degree;
+        p.m_max = o.medium_max_degree;
         p.max_rounds = max_rounds;
         p.X0 = (T*)(base + L.x0);
         p.X1 = (T*)(base + L.x1);
         p.colors_out = colors_out;
-        p.listA0 = (int32_t*)(base + L.l[0]);
-        p.listA1 = (int32_t*)(base + L.l[1]);
-        p.listA2 = (int32_t*)(base + L.l[2]);
-        p.listB0 = (int32_t*)(base + L.l[3]);
-        p.listB1 = (int32_t*)(base + L.l[4]);
-        p.listB2 = (int32_t*)(base + L.l[5]);
+        p.SA = (int32_t*)(base + L.S[0]);
+        p.MA = (int32_t*)(base + L.M[0]);
+        p.HA = (int32_t*)(base + L.H[0]);
+        p.HcA = (int32_t*)(base + L.Hc[0]);
+        p.OA = (int32_t*)(base + L.O[0]);
+        p.SB = (int32_t*)(base + L.S[1]);
+        p.MB = (int32_t*)(base + L.M[1]);
+        p.HB = (int32_t*)(base + L.H[1]);
+        p.HcB = (int32_t*)(base + L.Hc[1]);
+        p.OB = (int32_t*)(base + L.O[1]);
+        p.defer = (int32_t*)(base + L.defer);
+        p.hubs = (gc::HubRecord*)(base + L.hubs);
         p.st = st;
         p.round_sizes = (int32_t*)(base + L.rs);
         p.round_vol = (unsigned long long*)(base + L.rv);

@@ -17,9 +17,16 @@
 // pass 1 needs no color reads: v conflicts iff some neighbour precedes it,
 // and then its round-2 color is 2.
 //
-// Worklists are kept per degree bin (thread / warp / block per vertex).  A
-// vertex's bin never changes, so a vertex sent back is appended to the list
-// of its own bin with a warp-aggregated atomic.
+// Work is split into warp-sized tasks with at most 8 adjacency entries per
+// lane, all loads of a task issued before any is used:
+//   S bin (degree <= s_max <= 32): 4 lanes per vertex, 8 vertices per task;
+//   M bin (s_max < degree <= m_max <= 256): one vertex per task;
+//   H bin (degree > m_max): one 256-entry chunk of one vertex per task; the
+//     chunks of a vertex OR their conflict flag and color window into a
+//     per-vertex record, and the warp that finishes the last chunk decides.
+// Tasks are dealt to warps round-robin; no block-wide barrier is taken
+// inside a round.  A vertex's bin never changes, so a vertex sent back is
+// appended to the worklist of its own bin.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,7 +35,13 @@
 namespace gc {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBinThread = 0, kBinWarp = 1, kBinBlock = 2;
+constexpr int kBinS = 0, kBinM = 1, kBinH = 2;
+constexpr int kPerLane = 8;            // adjacency entries per lane and task
+constexpr int kGroup = 4;              // lanes per S-bin vertex
+constexpr int kSmallMaxLimit = kGroup * kPerLane;  // 32
+constexpr int kMedMaxLimit = 32 * kPerLane;        // 256
+constexpr int kChunk = 32 * kPerLane;              // 256 entries per H-bin task
+constexpr int kPass1Flat = 256;        // pass 1: larger degrees take the early-exit path
 
 // Status codes shared with gc.h (kept numerically equal).
 constexpr int kStatusOk = 0;
@@ -41,24 +54,31 @@ constexpr unsigned kBarrierMaxPolls = 1u << 26;
 
 struct Stats {
     int max_degree;
-    int bad;               // rowptr[0] != 0 or a negative degree
-    int nnz;               // rowptr[n]
-    int pad;
-    unsigned bin_count[3]; // vertices per degree bin
-    unsigned pad2;
+    int bad;                      // rowptr[0] != 0 or a negative degree
+    int nnz;                      // rowptr[n]
+    unsigned defer;               // vertices with degree > kPass1Flat
+    unsigned bin_count[3];        // vertices per degree bin
+    unsigned pad;
+    unsigned long long hub_chunks;  // sum over the H bin of ceil(degree / kChunk)
 };
 
 struct RoundState {
-    unsigned cnt[3][3];    // [k % 3][bin] = |U_k within bin|
-    unsigned tick[3];      // work tickets handed out in pass k, slot k % 3
-    unsigned defer_cnt[3]; // pass 1: vertices above the thread bin, per bin
-    unsigned defer_tick;
+    unsigned cnt[3][4];    // [k % 3] = {|U_k in S|, |U_k in M|, |U_k in H|, chunks of U_k in H}
+    unsigned defer_cnt;    // pass 1: vertices above kPass1Flat
     unsigned bar_count;
     unsigned bar_gen;
     int status;
     int rounds;
     int max_color;
-    int pad;
+    int pad[2];
+};
+
+// Per H-bin vertex of the current round (indexed by its worklist position).
+struct HubRecord {
+    unsigned mask[8];      // colors 1..256 seen by any chunk
+    unsigned conflict;
+    unsigned done;         // chunks finished
+    unsigned pad[6];
 };
 
 template <typename T>
@@ -67,33 +87,26 @@ struct Params {
     const int32_t* __restrict__ colidx;
     const uint32_t* __restrict__ prio;  // NULL = index priority
     int32_t n;
-    int32_t t1, t2;                     // degree bin limits
+    int32_t s_max, m_max;               // degree bin limits
     int32_t max_rounds;
     T* X0;
     T* X1;
     int32_t* colors_out;
-    int32_t* listA0; int32_t* listA1; int32_t* listA2;  // worklists of even k
-    int32_t* listB0; int32_t* listB1; int32_t* listB2;  // worklists of odd k
+    // worklists per parity (A: even k, B: odd k): S, M, H vertices,
+    // first chunk of each H vertex, owner position of each chunk
+    int32_t* SA; int32_t* MA; int32_t* HA; int32_t* HcA; int32_t* OA;
+    int32_t* SB; int32_t* MB; int32_t* HB; int32_t* HcB; int32_t* OB;
+    int32_t* defer;                     // pass 1 early-exit list
+    HubRecord* hubs;
     RoundState* st;
     int32_t* round_sizes;               // device telemetry, round_sizes[k-1] = |U_k|
     unsigned long long* round_vol;      // device telemetry, round_vol[k-1] = vol(U_k)
     int32_t round_cap;
 };
 
-// Add a block's share of vol(U_{r}) (sum of degrees) to round_vol[r-1].
-__device__ __forceinline__ void fold_volume(unsigned long long* round_vol, int32_t cap, int r,
-                                            unsigned long long vol) {
-    __shared__ unsigned long long s_vol;
-    if (threadIdx.x == 0) s_vol = 0;
-    __syncthreads();
-    if (vol) atomicAdd(&s_vol, vol);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_vol && r - 1 < cap) atomicAdd(&round_vol[r - 1], s_vol);
-}
-
 // ------------------------------------------------------------ helpers
 
-__device__ __forceinline__ unsigned ld_cg_u32(const unsigned* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // w precedes v: (prio[w], w) < (prio[v], v); pv = prio[v] (ignored if no prio).
 __device__ __forceinline__ bool precedes(const uint32_t* __restrict__ prio, int32_t w, int32_t v,
@@ -109,7 +122,7 @@ __device__ __forceinline__ bool precedes(const uint32_t* __restrict__ prio, int3
 __device__ __forceinline__ void warp_append(bool flag, int32_t v, int32_t* list, unsigned* cnt) {
     const unsigned ballot = __ballot_sync(kFull, flag);
     if (ballot == 0) return;
-    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lane = lane_id();
     const int leader = __ffs(ballot) - 1;
     unsigned base = 0;
     if ((int)lane == leader) base = atomicAdd(cnt, (unsigned)__popc(ballot));
@@ -117,7 +130,29 @@ __device__ __forceinline__ void warp_append(bool flag, int32_t v, int32_t* list,
     if (flag) list[base + __popc(ballot & ((1u << lane) - 1u))] = v;
 }
 
-// Bits of colors base+1 .. base+256 seen by one thread.
+// Where the next round's worklists go.
+struct NextLists {
+    int32_t* S; int32_t* M; int32_t* H; int32_t* Hc; int32_t* O;
+    unsigned* cnt;  // {S, M, H, H chunks} of the next round
+};
+
+// Append H-bin vertex v (degree d) to the next round and hand it its chunks.
+// Called by all lanes of a warp; lane `who` holds the vertex.
+__device__ __forceinline__ void warp_append_hub(const NextLists& nl, int32_t v, int32_t d) {
+    const unsigned nch = (unsigned)(d + kChunk - 1) / kChunk;
+    unsigned pos = 0, c0 = 0;
+    if (lane_id() == 0) {
+        pos = atomicAdd(&nl.cnt[kBinH], 1u);
+        c0 = atomicAdd(&nl.cnt[3], nch);
+        nl.H[pos] = v;
+        nl.Hc[pos] = (int32_t)c0;
+    }
+    pos = __shfl_sync(kFull, pos, 0);
+    c0 = __shfl_sync(kFull, c0, 0);
+    for (unsigned j = lane_id(); j < nch; j += 32) nl.O[c0 + j] = (int32_t)pos;
+}
+
+// Bits of colors base+1 .. base+256 seen by one lane.
 struct Mask256 {
     uint64_t w0, w1, w2, w3;
     __device__ __forceinline__ void clear() { w0 = w1 = w2 = w3 = 0; }
@@ -132,24 +167,53 @@ struct Mask256 {
             w3 |= (q == 3u) ? bit : 0ull;
         }
     }
-    __device__ __forceinline__ void warp_reduce(uint32_t r[8]) const {
-        r[0] = __reduce_or_sync(kFull, (uint32_t)w0);
-        r[1] = __reduce_or_sync(kFull, (uint32_t)(w0 >> 32));
-        r[2] = __reduce_or_sync(kFull, (uint32_t)w1);
-        r[3] = __reduce_or_sync(kFull, (uint32_t)(w1 >> 32));
-        r[4] = __reduce_or_sync(kFull, (uint32_t)w2);
-        r[5] = __reduce_or_sync(kFull, (uint32_t)(w2 >> 32));
-        r[6] = __reduce_or_sync(kFull, (uint32_t)w3);
-        r[7] = __reduce_or_sync(kFull, (uint32_t)(w3 >> 32));
+    // OR over the warp; every lane receives word `lane & 7` of the result.
+    __device__ __forceinline__ uint32_t warp_reduce_word() const {
+        const uint32_t r0 = __reduce_or_sync(kFull, (uint32_t)w0);
+        const uint32_t r1 = __reduce_or_sync(kFull, (uint32_t)(w0 >> 32));
+        const uint32_t r2 = __reduce_or_sync(kFull, (uint32_t)w1);
+        const uint32_t r3 = __reduce_or_sync(kFull, (uint32_t)(w1 >> 32));
+        const uint32_t r4 = __reduce_or_sync(kFull, (uint32_t)w2);
+        const uint32_t r5 = __reduce_or_sync(kFull, (uint32_t)(w2 >> 32));
+        const uint32_t r6 = __reduce_or_sync(kFull, (uint32_t)w3);
+        const uint32_t r7 = __reduce_or_sync(kFull, (uint32_t)(w3 >> 32));
+        const unsigned q = lane_id() & 7u;
+        uint32_t r = r0;
+        r = q == 1u ? r1 : r;
+        r = q == 2u ? r2 : r;
+        r = q == 3u ? r3 : r;
+        r = q == 4u ? r4 : r;
+        r = q == 5u ? r5 : r;
+        r = q == 6u ? r6 : r;
+        r = q == 7u ? r7 : r;
+        return r;
     }
 };
 
-// Index of the first clear bit of an 8-word mask, or -1 if all 256 are set.
-__device__ __forceinline__ int first_clear(const uint32_t r[8]) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (r[j] != 0xffffffffu) return j * 32 + __ffs(~r[j]) - 1;
-    return -1;
+// First clear bit of the 256-bit window whose word q sits in lanes with
+// (lane & 7) == q; -1 if all set.  All lanes call it and get the same value.
+__device__ __forceinline__ int window_first_clear(uint32_t word) {
+    const unsigned notfull = __ballot_sync(kFull, lane_id() < 8u && word != 0xffffffffu);
+    if (notfull == 0) return -1;
+    const int q = __ffs(notfull) - 1;
+    const uint32_t wq = __shfl_sync(kFull, word, q);
+    return q * 32 + __ffs(~wq) - 1;
+}
+
+// First fit beyond the first window: rescan adj(v) for windows base+1 ..
+// until one has a free color.  Terminates: a full window of 256 colors needs
+// 256 more neighbours, and first fit never exceeds degree + 1.
+template <typename T>
+__device__ __forceinline__ unsigned rescan_first_fit(const int32_t* __restrict__ colidx, const T* Xc,
+                                                     int32_t b, int32_t e) {
+    for (unsigned base = 256u;; base += 256u) {
+        Mask256 m;
+        m.clear();
+        for (int32_t i = b + (int32_t)lane_id(); i < e; i += 32)
+            m.set((unsigned)__ldcg(Xc + __ldg(colidx + i)) - 1u - base);
+        const int ff = window_first_clear(m.warp_reduce_word());
+        if (ff >= 0) return base + (unsigned)ff + 1u;
+    }
 }
 
 // --------------------------------------------------- bounded grid barrier
@@ -179,7 +243,7 @@ __device__ __forceinline__ bool grid_barrier(RoundState* st) {
             const unsigned long long t0 = globaltimer_ns();
             unsigned polls = 0;
             while (*vgen == gen) {
-                __nanosleep(64);
+                __nanosleep(32);
                 if (++polls >= kBarrierMaxPolls || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
                     atomicExch(&st->status, kStatusTimeout);
                     ok = 0;
@@ -196,160 +260,212 @@ __device__ __forceinline__ bool grid_barrier(RoundState* st) {
 }
 
 __device__ __forceinline__ void fold_max_color(RoundState* st, int maxc) {
-    __shared__ int s_max;
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
     const int m = __reduce_max_sync(kFull, maxc);
-    if ((threadIdx.x & 31u) == 0 && m > 0) atomicMax(&s_max, m);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_max > 0) atomicMax(&st->max_color, s_max);
+    if (lane_id() == 0 && m > 0) atomicMax(&st->max_color, m);
+}
+
+// Add a warp's share of vol(U_r) (sum of degrees) to round_vol[r-1].
+__device__ __forceinline__ void fold_volume(unsigned long long* round_vol, int32_t cap, int r,
+                                            unsigned vol) {
+    const unsigned s = __reduce_add_sync(kFull, vol);
+    if (lane_id() == 0 && s && r - 1 < cap) atomicAdd(&round_vol[r - 1], (unsigned long long)s);
+}
+
+__device__ __forceinline__ int bin_of(int32_t d, int32_t s_max, int32_t m_max) {
+    return d <= s_max ? kBinS : (d <= m_max ? kBinM : kBinH);
 }
 
 // ------------------------------------------------------------ setup scan
 
-// Degree statistics: max degree, vertices per bin, shape checks of rowptr.
-__global__ void stats_kernel(const int32_t* __restrict__ rowptr, int32_t n, int32_t t1, int32_t t2,
-                             Stats* s) {
-    __shared__ unsigned s_bins[3];
-    __shared__ int s_max, s_bad;
-    if (threadIdx.x < 3) s_bins[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { s_max = 0; s_bad = 0; }
-    __syncthreads();
+// Degree statistics: max degree, vertices per bin, hub chunks, rowptr checks.
+__global__ void stats_kernel(const int32_t* __restrict__ rowptr, int32_t n, int32_t s_max,
+                             int32_t m_max, Stats* s) {
     int mx = 0, bad = 0;
-    unsigned b0 = 0, b1 = 0, b2 = 0;
+    unsigned b0 = 0, b1 = 0, b2 = 0, df = 0;
+    unsigned long long ch = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t d = __ldg(rowptr + v + 1) - __ldg(rowptr + v);
-        if (d < 0) bad = 1;
+        if (d < 0) { bad = 1; continue; }
         mx = max(mx, d);
-        b0 += (d <= t1);
-        b1 += (d > t1 && d <= t2);
-        b2 += (d > t2);
+        const int bin = bin_of(d, s_max, m_max);
+        b0 += bin == kBinS;
+        b1 += bin == kBinM;
+        b2 += bin == kBinH;
+        df += d > kPass1Flat;
+        if (bin == kBinH) ch += (unsigned long long)((d + kChunk - 1) / kChunk);
     }
-    atomicMax(&s_max, mx);
-    if (bad) s_bad = 1;
-    if (b0) atomicAdd(&s_bins[0], b0);
-    if (b1) atomicAdd(&s_bins[1], b1);
-    if (b2) atomicAdd(&s_bins[2], b2);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicMax(&s->max_degree, s_max);
-        if (s_bad) s->bad = 1;
-        for (int b = 0; b < 3; ++b)
-            if (s_bins[b]) atomicAdd(&s->bin_count[b], s_bins[b]);
-        if (blockIdx.x == 0) {
-            if (__ldg(rowptr) != 0) s->bad = 1;
-            s->nnz = __ldg(rowptr + n);
-        }
+    mx = __reduce_max_sync(kFull, mx);
+    bad = __reduce_or_sync(kFull, (unsigned)bad);
+    b0 = __reduce_add_sync(kFull, b0);
+    b1 = __reduce_add_sync(kFull, b1);
+    b2 = __reduce_add_sync(kFull, b2);
+    df = __reduce_add_sync(kFull, df);
+    if (lane_id() == 0) {
+        atomicMax(&s->max_degree, mx);
+        if (bad) s->bad = 1;
+        if (b0) atomicAdd(&s->bin_count[0], b0);
+        if (b1) atomicAdd(&s->bin_count[1], b1);
+        if (b2) atomicAdd(&s->bin_count[2], b2);
+        if (df) atomicAdd(&s->defer, df);
+    }
+    for (int o = 16; o > 0; o >>= 1) ch += __shfl_xor_sync(kFull, ch, o);
+    if (lane_id() == 0 && ch) atomicAdd(&s->hub_chunks, ch);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (__ldg(rowptr) != 0) s->bad = 1;
+        s->nnz = __ldg(rowptr + n);
     }
 }
 
 // ------------------------------------------------------------- pass 1
 
-// Thread-bin vertices decide round 1 here; larger ones are deferred to
-// pass1_big_kernel.  Round 1 is closed form: C_1 = 1 everywhere, so v
-// conflicts iff some neighbour precedes it (early exit), and C_2[v] = 2.
+// Outcome of round 1 for v: C_2[v] = 2 if it conflicts (then it joins U_2),
+// else v keeps color 1 for good.
 template <typename T>
-__global__ void __launch_bounds__(256) pass1_thread_kernel(Params<T> p) {
-    RoundState* st = p.st;
-    int maxc = 0;
-    unsigned long long vol = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < p.n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vv = base + threadIdx.x;
-        const bool valid = vv < p.n;
-        const int32_t v = valid ? (int32_t)vv : 0;
-        bool conflict = false, defer_w = false, defer_b = false;
-        if (valid) {
-            const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-            const int32_t d = e - b;
-            if (d > p.t1) {
-                defer_w = d <= p.t2;
-                defer_b = !defer_w;
-            } else {
-                const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-                for (int32_t i = b; i < e; ++i)
-                    if (precedes(p.prio, __ldg(p.colidx + i), v, pv)) { conflict = true; break; }
-                if (conflict) vol += (unsigned long long)d;
-                p.X0[v] = conflict ? (T)2 : (T)1;
-                if (!conflict) {
-                    p.X1[v] = (T)1;
-                    p.colors_out[v] = 1;
-                    maxc = 1;
-                }
-            }
-        }
-        warp_append(conflict, v, p.listA0, &st->cnt[2][kBinThread]);
-        warp_append(defer_w, v, p.listB1, &st->defer_cnt[kBinWarp]);
-        warp_append(defer_b, v, p.listB2, &st->defer_cnt[kBinBlock]);
-    }
-    fold_max_color(st, maxc);
-    fold_volume(p.round_vol, p.round_cap, 2, vol);
-}
-
-// Round 1 for the deferred warp- and block-bin vertices, early exit on the
-// first preceding neighbour.
-template <typename T>
-__device__ __forceinline__ void pass1_finish(const Params<T>& p, int32_t v, int32_t deg, bool conflict,
-                                             int bin, int& maxc, unsigned long long& vol) {
+__device__ __forceinline__ void pass1_write(const Params<T>& p, int32_t v, bool conflict, int& maxc) {
     p.X0[v] = conflict ? (T)2 : (T)1;
     if (!conflict) {
         p.X1[v] = (T)1;
         p.colors_out[v] = 1;
         maxc = 1;
-    } else {
-        int32_t* list = bin == kBinWarp ? p.listA1 : p.listA2;
-        list[atomicAdd(&p.st->cnt[2][bin], 1u)] = v;
-        vol += (unsigned long long)deg;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) pass1_big_kernel(Params<T> p) {
-    __shared__ unsigned s_task;
-    RoundState* st = p.st;
-    const unsigned nW = __ldcg(&st->defer_cnt[kBinWarp]);
-    const unsigned nB = __ldcg(&st->defer_cnt[kBinBlock]);
-    const unsigned warps = blockDim.x >> 5;
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const unsigned tasksW = (nW + warps - 1) / warps;
-    const unsigned total = nB + tasksW;
+__device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
+    NextLists nl;
+    nl.S = p.SA; nl.M = p.MA; nl.H = p.HA; nl.Hc = p.HcA; nl.O = p.OA;
+    nl.cnt = p.st->cnt[2];
+    return nl;
+}
+
+// Round 1 on 32 consecutive vertices per task.  Their adjacency entries
+// (rows of degree <= kPass1Flat) are read as one flat, coalesced range;
+// lane l of batch u handles flat entry F0 + 32u + l, finds its row by a
+// binary search over the rows' running totals, and the per-row conflict
+// flag is gathered from the batch ballot.  Larger rows go to the early-exit
+// list.
+template <typename T>
+__global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
+    const unsigned lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntasks = ((int64_t)p.n + 31) / 32;
+    const NextLists nl = pass1_next(p);
     int maxc = 0;
-    unsigned long long vol = 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(&st->defer_tick, 1u);
-        __syncthreads();
-        unsigned t = s_task;
-        __syncthreads();
-        if (t >= total) break;
-        if (t < nB) {
-            const int32_t v = __ldcg(p.listB2 + t);
-            const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-            const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-            bool conflict = false;
-            for (int32_t c = b; c < e; c += blockDim.x) {
-                const int32_t i = c + threadIdx.x;
-                const bool hit = i < e && precedes(p.prio, __ldg(p.colidx + i), v, pv);
-                if (__syncthreads_or(hit)) { conflict = true; break; }
-            }
-            if (threadIdx.x == 0) pass1_finish(p, v, e - b, conflict, kBinBlock, maxc, vol);
-        } else {
-            const unsigned i = (t - nB) * warps + warp;
-            if (i < nW) {
-                const int32_t v = __ldcg(p.listB1 + i);
-                const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-                const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-                bool conflict = false;
-                for (int32_t c = b; c < e; c += 32) {
-                    const int32_t j = c + (int32_t)lane;
-                    const bool hit = j < e && precedes(p.prio, __ldg(p.colidx + j), v, pv);
-                    if (__any_sync(kFull, hit)) { conflict = true; break; }
+    unsigned vol = 0;
+    for (int64_t t = gw; t < ntasks; t += W) {
+        const int64_t vv = t * 32 + lane;
+        const bool valid = vv < p.n;
+        const int32_t v = valid ? (int32_t)vv : 0;
+        const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
+        const int32_t d = valid ? __ldg(p.rowptr + v + 1) - b : 0;
+        const bool defer = d > kPass1Flat;
+        const int32_t eff = defer ? 0 : d;
+        const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
+        int32_t incl = eff;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t x = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += x;
+        }
+        const int32_t off = incl - eff;
+        const int32_t D = __shfl_sync(kFull, incl, 31);
+        bool hit = false;
+        for (int32_t F0 = 0; F0 < D; F0 += 32 * 4) {
+            int32_t w[4], own[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t f = F0 + 32 * u + (int32_t)lane;
+                // first row whose running total exceeds f
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const int mid = (lo + hi) >> 1;
+                    const int32_t val = __shfl_sync(kFull, incl, mid);
+                    if (val > f) hi = mid; else lo = mid + 1;
                 }
-                if (lane == 0) pass1_finish(p, v, e - b, conflict, kBinWarp, maxc, vol);
+                own[u] = lo;
+                const int32_t ob = __shfl_sync(kFull, b, lo);
+                const int32_t oo = __shfl_sync(kFull, off, lo);
+                w[u] = f < D ? __ldg(p.colidx + ob + (f - oo)) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t f = F0 + 32 * u + (int32_t)lane;
+                const uint32_t opv = __shfl_sync(kFull, pv, own[u]);
+                const bool h = f < D && precedes(p.prio, w[u], (int32_t)(t * 32 + own[u]), opv);
+                const unsigned ballot = __ballot_sync(kFull, h);
+                const int32_t lo = max(0, min(32, off - (F0 + 32 * u)));
+                const int32_t hi = max(0, min(32, off + eff - (F0 + 32 * u)));
+                if (hi > lo) {
+                    const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
+                    if ((ballot >> lo) & bits) hit = true;
+                }
+            }
+        }
+        if (valid && !defer) {
+            pass1_write(p, v, hit, maxc);
+            if (hit) vol += (unsigned)d;
+        }
+        const int bin = bin_of(d, p.s_max, p.m_max);
+        const bool go = valid && !defer && hit;
+        warp_append(go && bin == kBinS, v, nl.S, &nl.cnt[kBinS]);
+        warp_append(go && bin == kBinM, v, nl.M, &nl.cnt[kBinM]);
+        // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
+        unsigned hubs = __ballot_sync(kFull, go && bin == kBinH);
+        while (hubs) {
+            const int j = __ffs(hubs) - 1;
+            hubs &= hubs - 1;
+            warp_append_hub(nl, __shfl_sync(kFull, v, j), __shfl_sync(kFull, d, j));
+        }
+        warp_append(valid && defer, v, p.defer, &p.st->defer_cnt);
+    }
+    fold_max_color(p.st, maxc);
+    fold_volume(p.round_vol, p.round_cap, 2, vol);
+}
+
+// Round 1 for rows longer than kPass1Flat: one warp per vertex, 128
+// entries per step, stop at the first preceding neighbour.
+template <typename T>
+__global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
+    const unsigned lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned nd = __ldcg(&p.st->defer_cnt);
+    const NextLists nl = pass1_next(p);
+    int maxc = 0;
+    unsigned vol = 0;
+    for (int64_t t = gw; t < nd; t += W) {
+        const int32_t v = __ldcg(p.defer + t);
+        const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
+        const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
+        bool conflict = false;
+        for (int32_t c = b; c < e && !conflict; c += 128) {
+            int32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t i = c + 32 * u + (int32_t)lane;
+                w[u] = i < e ? __ldg(p.colidx + i) : -1;
+            }
+            bool h = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) h |= w[u] >= 0 && precedes(p.prio, w[u], v, pv);
+            conflict = __any_sync(kFull, h);
+        }
+        if (lane == 0) pass1_write(p, v, conflict, maxc);
+        if (conflict) {
+            const int bin = bin_of(e - b, p.s_max, p.m_max);
+            if (lane == 0) vol += (unsigned)(e - b);
+            if (bin == kBinH) {
+                warp_append_hub(nl, v, e - b);
+            } else if (lane == 0) {
+                int32_t* list = bin == kBinM ? nl.M : nl.S;
+                list[atomicAdd(&nl.cnt[bin], 1u)] = v;
             }
         }
     }
-    fold_max_color(st, maxc);
+    fold_max_color(p.st, maxc);
     fold_volume(p.round_vol, p.round_cap, 2, vol);
 }
 
@@ -359,9 +475,8 @@ template <typename T>
 struct PassIO {
     const T* Xc;        // C_k
     T* Xn;              // receives C_{k+1} (conflicting) or the final color (settled)
-    const int32_t* cur0; const int32_t* cur1; const int32_t* cur2;
-    int32_t* nxt0; int32_t* nxt1; int32_t* nxt2;
-    unsigned* ncnt;     // st->cnt[(k + 1) % 3]
+    const int32_t* S; const int32_t* M; const int32_t* H; const int32_t* Hc; const int32_t* O;
+    NextLists next;
 };
 
 template <typename T>
@@ -370,182 +485,196 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     const bool odd = (k & 1) != 0;
     io.Xc = odd ? p.X1 : p.X0;
     io.Xn = odd ? p.X0 : p.X1;
-    io.cur0 = odd ? p.listB0 : p.listA0;
-    io.cur1 = odd ? p.listB1 : p.listA1;
-    io.cur2 = odd ? p.listB2 : p.listA2;
-    io.nxt0 = odd ? p.listA0 : p.listB0;
-    io.nxt1 = odd ? p.listA1 : p.listB1;
-    io.nxt2 = odd ? p.listA2 : p.listB2;
-    io.ncnt = p.st->cnt[(k + 1) % 3];
+    io.S = odd ? p.SB : p.SA;
+    io.M = odd ? p.MB : p.MA;
+    io.H = odd ? p.HB : p.HA;
+    io.Hc = odd ? p.HcB : p.HcA;
+    io.O = odd ? p.OB : p.OA;
+    io.next.S = odd ? p.SA : p.SB;
+    io.next.M = odd ? p.MA : p.MB;
+    io.next.H = odd ? p.HA : p.HB;
+    io.next.Hc = odd ? p.HcA : p.HcB;
+    io.next.O = odd ? p.OA : p.OB;
+    io.next.cnt = p.st->cnt[(k + 1) % 3];
     return io;
 }
 
-// Thread per vertex (degree <= t1 <= 63): one 64-bit mask holds every color
-// that can matter, since first fit never exceeds degree + 1.
 template <typename T>
-__device__ __forceinline__ void thread_vertex(const Params<T>& p, const PassIO<T>& io, int32_t v,
-                                              bool valid, int& maxc, unsigned long long& vol) {
-    bool conflict = false;
-    if (valid) {
-        const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-        const T cv = __ldcg(io.Xc + v);
-        const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-        uint64_t mask = 0;
-#pragma unroll 4
-        for (int32_t i = b; i < e; ++i) {
-            const int32_t w = __ldg(p.colidx + i);
-            const T c = __ldcg(io.Xc + w);
-            if (c == cv && precedes(p.prio, w, v, pv)) conflict = true;
-            const unsigned idx = (unsigned)c - 1u;
-            mask |= (idx < 64u) ? (1ull << idx) : 0ull;
+__device__ __forceinline__ void settle(const Params<T>& p, const PassIO<T>& io, int32_t v, T cv) {
+    io.Xn[v] = cv;
+    p.colors_out[v] = (int32_t)cv;
+}
+
+// S bin: 8 vertices per task, 4 lanes per vertex, <= 8 entries per lane.
+// First fit <= degree + 1 <= 33, so bits 0..62 of one 64-bit word hold every
+// color that matters; bit 63 carries the conflict flag through the reduction.
+template <typename T>
+__device__ __forceinline__ void small_group(const Params<T>& p, const PassIO<T>& io, unsigned t,
+                                            unsigned nS, int& maxc, unsigned& vol) {
+    const unsigned lane = lane_id();
+    const unsigned q = lane & (kGroup - 1);
+    const unsigned i = t * (32 / kGroup) + (lane / kGroup);
+    const bool valid = i < nS;
+    const int32_t v = valid ? __ldcg(io.S + i) : 0;
+    const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
+    const int32_t e = valid ? __ldg(p.rowptr + v + 1) : 0;
+    const T cv = valid ? __ldcg(io.Xc + v) : (T)0;
+    const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
+    int32_t w[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        const int32_t j = b + (int32_t)q + kGroup * u;
+        w[u] = j < e ? __ldg(p.colidx + j) : -1;
+    }
+    T c[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
+    uint64_t mask = 0;
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        if (w[u] >= 0) {
+            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) mask |= 1ull << 63;
+            const unsigned idx = (unsigned)c[u] - 1u;
+            mask |= idx < 63u ? (1ull << idx) : 0ull;
         }
+    }
+    mask |= __shfl_xor_sync(kFull, mask, 1);
+    mask |= __shfl_xor_sync(kFull, mask, 2);
+    const bool conflict = valid && (mask >> 63) != 0;
+    if (valid && q == 0) {
         if (conflict) {
             io.Xn[v] = (T)__ffsll((long long)~mask);
-            vol += (unsigned long long)(e - b);
+            vol += (unsigned)(e - b);
         } else {
-            io.Xn[v] = cv;
-            p.colors_out[v] = (int32_t)cv;
+            settle(p, io, v, cv);
             maxc = max(maxc, (int)cv);
         }
     }
-    warp_append(conflict, v, io.nxt0, &io.ncnt[kBinThread]);
+    warp_append(conflict && q == 0, v, io.next.S, &io.next.cnt[kBinS]);
 }
 
-// Warp per vertex: lanes stride over adj(v); colors in a 256-wide window are
-// OR-reduced across the warp; a full window moves on and rescans.
+// M bin: one vertex per task, <= 8 entries per lane.
 template <typename T>
-__device__ __forceinline__ void warp_vertex(const Params<T>& p, const PassIO<T>& io, int32_t v,
-                                            int& maxc, unsigned long long& vol) {
-    const int32_t lane = (int32_t)(threadIdx.x & 31u);
+__device__ __forceinline__ void medium_vertex(const Params<T>& p, const PassIO<T>& io, int32_t v,
+                                              int& maxc, unsigned& vol) {
+    const unsigned lane = lane_id();
     const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
     const T cv = __ldcg(io.Xc + v);
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
+    int32_t w[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        const int32_t j = b + (int32_t)lane + 32 * u;
+        w[u] = j < e ? __ldg(p.colidx + j) : -1;
+    }
+    T c[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
     bool conflict = false;
     Mask256 m;
     m.clear();
-#pragma unroll 2
-    for (int32_t i = b + lane; i < e; i += 32) {
-        const int32_t w = __ldg(p.colidx + i);
-        const T c = __ldcg(io.Xc + w);
-        if (c == cv && precedes(p.prio, w, v, pv)) conflict = true;
-        m.set((unsigned)c - 1u);
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        if (w[u] >= 0) {
+            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+            m.set((unsigned)c[u] - 1u);
+        }
     }
     if (!__any_sync(kFull, conflict)) {
-        if (lane == 0) {
-            io.Xn[v] = cv;
-            p.colors_out[v] = (int32_t)cv;
-        }
+        if (lane == 0) settle(p, io, v, cv);
         maxc = max(maxc, (int)cv);
         return;
     }
-    uint32_t r[8];
-    m.warp_reduce(r);
-    int ff = first_clear(r);
-    unsigned base = 0;
-    while (ff < 0) {
-        base += 256u;
-        m.clear();
-        for (int32_t i = b + lane; i < e; i += 32) {
-            const T c = __ldcg(io.Xc + __ldg(p.colidx + i));
-            m.set((unsigned)c - 1u - base);
-        }
-        m.warp_reduce(r);
-        ff = first_clear(r);
-    }
+    int ff = window_first_clear(m.warp_reduce_word());
+    const unsigned color = ff >= 0 ? (unsigned)ff + 1u : rescan_first_fit(p.colidx, io.Xc, b, e);
     if (lane == 0) {
-        io.Xn[v] = (T)(base + (unsigned)ff + 1u);
-        io.nxt1[atomicAdd(&io.ncnt[kBinWarp], 1u)] = v;
-        vol += (unsigned long long)(e - b);
+        io.Xn[v] = (T)color;
+        io.next.M[atomicAdd(&io.next.cnt[kBinM], 1u)] = v;
+        vol += (unsigned)(e - b);
     }
 }
 
-// Block per vertex: as the warp form, with the warps' masks OR-ed in shared memory.
+// H bin: chunk t of the vertex at worklist position O[t].  The warp that
+// completes the vertex's last chunk decides it and clears its record.
 template <typename T>
-__device__ __forceinline__ void block_vertex(const Params<T>& p, const PassIO<T>& io, int32_t v,
-                                             int& maxc, unsigned long long& vol, uint32_t* s_mask) {
+__device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, unsigned t,
+                                          int& maxc, unsigned& vol) {
+    const unsigned lane = lane_id();
+    const int32_t pos = __ldcg(io.O + t);
+    const int32_t v = __ldcg(io.H + pos);
+    const int32_t c0 = __ldcg(io.Hc + pos);
     const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
+    const int32_t lo = b + ((int32_t)t - c0) * kChunk;
+    const int32_t hi = min(e, lo + kChunk);
     const T cv = __ldcg(io.Xc + v);
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
+    int32_t w[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        const int32_t j = lo + (int32_t)lane + 32 * u;
+        w[u] = j < hi ? __ldg(p.colidx + j) : -1;
+    }
+    T c[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
     bool conflict = false;
     Mask256 m;
     m.clear();
-#pragma unroll 2
-    for (int32_t i = b + (int32_t)threadIdx.x; i < e; i += (int32_t)blockDim.x) {
-        const int32_t w = __ldg(p.colidx + i);
-        const T c = __ldcg(io.Xc + w);
-        if (c == cv && precedes(p.prio, w, v, pv)) conflict = true;
-        m.set((unsigned)c - 1u);
-    }
-    if (!__syncthreads_or(conflict)) {
-        if (threadIdx.x == 0) {
-            io.Xn[v] = cv;
-            p.colors_out[v] = (int32_t)cv;
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        if (w[u] >= 0) {
+            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+            m.set((unsigned)c[u] - 1u);
         }
+    }
+    const bool any_conflict = __any_sync(kFull, conflict);
+    const uint32_t word = m.warp_reduce_word();
+    HubRecord* rec = p.hubs + pos;
+    if (lane < 8u && word) atomicOr(&rec->mask[lane], word);
+    if (lane == 0 && any_conflict) atomicOr(&rec->conflict, 1u);
+    __threadfence();
+    const unsigned nch = (unsigned)(e - b + kChunk - 1) / kChunk;
+    unsigned done = 0;
+    if (lane == 0) done = atomicAdd(&rec->done, 1u);
+    done = __shfl_sync(kFull, done, 0);
+    if (done != nch - 1) return;
+    // last chunk of v: decide
+    __threadfence();
+    const uint32_t all = lane < 8u ? __ldcg(&rec->mask[lane & 7u]) : 0u;
+    const bool conf = __ldcg(&rec->conflict) != 0u;
+    if (lane < 16u) ((unsigned*)rec)[lane] = 0u;  // reset for the next round
+    if (!conf) {
+        if (lane == 0) settle(p, io, v, cv);
         maxc = max(maxc, (int)cv);
         return;
     }
-    unsigned base = 0;
-    for (;;) {
-        if (threadIdx.x < 8) s_mask[threadIdx.x] = 0u;
-        __syncthreads();
-        uint32_t r[8];
-        m.warp_reduce(r);
-        if ((threadIdx.x & 31u) == 0) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (r[j]) atomicOr(&s_mask[j], r[j]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) r[j] = s_mask[j];
-        const int ff = first_clear(r);
-        __syncthreads();
-        if (ff >= 0) {
-            if (threadIdx.x == 0) {
-                io.Xn[v] = (T)(base + (unsigned)ff + 1u);
-                io.nxt2[atomicAdd(&io.ncnt[kBinBlock], 1u)] = v;
-                vol += (unsigned long long)(e - b);
-            }
-            return;
-        }
-        base += 256u;
-        m.clear();
-        for (int32_t i = b + (int32_t)threadIdx.x; i < e; i += (int32_t)blockDim.x) {
-            const T c = __ldcg(io.Xc + __ldg(p.colidx + i));
-            m.set((unsigned)c - 1u - base);
-        }
+    const int ff = window_first_clear(all);
+    const unsigned color = ff >= 0 ? (unsigned)ff + 1u : rescan_first_fit(p.colidx, io.Xc, b, e);
+    if (lane == 0) {
+        io.Xn[v] = (T)color;
+        vol += (unsigned)(e - b);
     }
+    warp_append_hub(io.next, v, e - b);
 }
 
-// One fused pass over U_k.  Work is handed out by ticket: block-bin vertices
-// first (largest first helps balance), then warp-bin chunks (one vertex per
-// warp), then thread-bin chunks (one vertex per thread).
+// One fused pass over U_k.  Task t: first the H-bin chunks, then the M-bin
+// vertices, then groups of 8 S-bin vertices; warp w takes t = w, w + W, ...
 template <typename T>
-__device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nL, unsigned nM,
-                                         unsigned nH, int& maxc, unsigned* s_task, uint32_t* s_mask) {
+__device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
+                                         unsigned nHC, int& maxc) {
     const PassIO<T> io = pass_io(p, k);
-    unsigned* tick = &p.st->tick[k % 3];
-    const unsigned warps = blockDim.x >> 5;
-    const unsigned tasksM = (nM + warps - 1) / warps;
-    const unsigned tasksL = (nL + blockDim.x - 1) / blockDim.x;
-    const unsigned total = nH + tasksM + tasksL;
-    unsigned long long vol = 0;  // vol(U_{k+1}) share of this thread
-    for (;;) {
-        if (threadIdx.x == 0) *s_task = atomicAdd(tick, 1u);
-        __syncthreads();
-        unsigned t = *s_task;
-        __syncthreads();
-        if (t >= total) break;
-        if (t < nH) {
-            block_vertex(p, io, __ldcg(io.cur2 + t), maxc, vol, s_mask);
-        } else if ((t -= nH) < tasksM) {
-            const unsigned i = t * warps + (threadIdx.x >> 5);
-            if (i < nM) warp_vertex(p, io, __ldcg(io.cur1 + i), maxc, vol);
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned W = (gridDim.x * blockDim.x) >> 5;
+    const unsigned groups = (nS + (32 / kGroup) - 1) / (32 / kGroup);
+    const unsigned total = nHC + nM + groups;
+    unsigned vol = 0;  // this lane's share of vol(U_{k+1})
+    for (unsigned t = gw; t < total; t += W) {
+        if (t < nHC) {
+            hub_chunk(p, io, t, maxc, vol);
+        } else if (t - nHC < nM) {
+            medium_vertex(p, io, __ldcg(io.M + (t - nHC)), maxc, vol);
         } else {
-            t -= tasksM;
-            const unsigned i = t * blockDim.x + threadIdx.x;
-            const bool valid = i < nL;
-            thread_vertex(p, io, valid ? __ldcg(io.cur0 + i) : 0, valid, maxc, vol);
+            small_group(p, io, t - nHC - nM, nS, maxc, vol);
         }
     }
     fold_volume(p.round_vol, p.round_cap, k + 1, vol);
@@ -555,15 +684,14 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nL,
 // separates the rounds.  Every block reads the same counts after a barrier,
 // so all blocks leave the loop in the same round.
 template <typename T>
-__global__ void __launch_bounds__(512) rounds_persistent_kernel(Params<T> p) {
-    __shared__ unsigned s_task;
-    __shared__ uint32_t s_mask[8];
+__global__ void __launch_bounds__(256) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
     for (int k = 2;; ++k) {
         const unsigned* c = st->cnt[k % 3];
-        const unsigned nL = ld_cg_u32(c + 0), nM = ld_cg_u32(c + 1), nH = ld_cg_u32(c + 2);
-        const unsigned size = nL + nM + nH;
+        const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nH = __ldcg(c + 2),
+                       nHC = __ldcg(c + 3);
+        const unsigned size = nS + nM + nH;
         if (size == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) st->rounds = k - 1;
             break;
@@ -577,11 +705,10 @@ __global__ void __launch_bounds__(512) rounds_persistent_kernel(Params<T> p) {
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             unsigned* z = st->cnt[(k + 2) % 3];
-            z[0] = z[1] = z[2] = 0u;
-            st->tick[(k + 2) % 3] = 0u;
+            z[0] = z[1] = z[2] = z[3] = 0u;
             if (k - 1 < p.round_cap) p.round_sizes[k - 1] = (int32_t)size;
         }
-        run_pass(p, k, nL, nM, nH, maxc, &s_task, s_mask);
+        run_pass(p, k, nS, nM, nHC, maxc);
         if (!grid_barrier(st)) break;
     }
     fold_max_color(st, maxc);
@@ -589,12 +716,10 @@ __global__ void __launch_bounds__(512) rounds_persistent_kernel(Params<T> p) {
 
 // One pass per launch (loop mode 1): counts come from the host.
 template <typename T>
-__global__ void __launch_bounds__(512) round_kernel(Params<T> p, int k, unsigned nL, unsigned nM,
-                                                    unsigned nH) {
-    __shared__ unsigned s_task;
-    __shared__ uint32_t s_mask[8];
+__global__ void __launch_bounds__(256) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
+                                                    unsigned nHC) {
     int maxc = 0;
-    run_pass(p, k, nL, nM, nH, maxc, &s_task, s_mask);
+    run_pass(p, k, nS, nM, nHC, maxc);
     fold_max_color(p.st, maxc);
 }
 
@@ -619,7 +744,7 @@ struct ValidateOut {
 // multiset E and of its transpose (equal when E is symmetric).
 __global__ void validate_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                 int32_t n, ValidateOut* out) {
-    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long f = 0, g = 0;

@@ -78,11 +78,11 @@ def test_parity_with_priority(gcpkg, make):
     {"loop_mode": 1},
     {"color_bits": 32},
     {"color_bits": 32, "loop_mode": 1},
-    {"thread_max_degree": 1, "warp_max_degree": 1},      # everything block-per-vertex
-    {"thread_max_degree": 63, "warp_max_degree": 63},    # no warp bin
-    {"thread_max_degree": 1, "warp_max_degree": 100000}, # everything warp-per-vertex
+    {"small_max_degree": 1, "medium_max_degree": 1},     # nearly everything in 256-entry chunks
+    {"small_max_degree": 32, "medium_max_degree": 32},   # no medium bin
+    {"small_max_degree": 1, "medium_max_degree": 256},   # nearly everything warp-per-vertex
+    {"small_max_degree": 5, "medium_max_degree": 40},
     {"block_threads": 128},
-    {"block_threads": 512},
 ])
 def test_parity_launch_variants(gcpkg, opts):
     for g in [gg.rmat(13, 8, gg.RMAT_B, 7), gg.complete(300), gg.gnm(3000, 30000, 9)]:
@@ -90,11 +90,11 @@ def test_parity_launch_variants(gcpkg, opts):
 
 
 def test_degrees_at_bin_edges(gcpkg):
-    """Vertices with degree exactly t1, t1+1, t2, t2+1 (hubs joined to a path)."""
-    t1, t2 = 24, 2048
+    """Vertices with degree exactly at and just above each bin limit and chunk
+    size (32, 33, 256, 257, 512, 513), plus long rows (hubs joined to a path)."""
     n = 6000
     u, v = list(range(n - 1)), list(range(1, n))
-    spec = [(10, t1), (20, t1 + 1), (30, t2), (40, t2 + 1), (50, 63), (60, 64), (70, 257)]
+    spec = [(10, 32), (20, 33), (30, 256), (40, 257), (50, 512), (60, 513), (70, 2049)]
     hubs = {h for h, _ in spec}
     for hub, d in spec:
         nb = [(hub + 100 + 37 * j) % n for j in range(4 * d)]
@@ -105,13 +105,15 @@ def test_degrees_at_bin_edges(gcpkg):
     assert [int(g.degrees[h]) for h, _ in spec] == [d for _, d in spec]
     _check(gcpkg, g)
     _check(gcpkg, g, options={"color_bits": 32})
+    _check(gcpkg, g, options={"small_max_degree": 31, "medium_max_degree": 255})
 
 
 def test_many_colors_window_rescan(gcpkg):
     """K_600: first-fit colors beyond the 64- and 256-wide mask windows."""
     res = _check(gcpkg, gg.complete(600))
     assert res.ncolors == 600
-    res = _check(gcpkg, gg.complete(600), options={"thread_max_degree": 1, "warp_max_degree": 100000})
+    res = _check(gcpkg, gg.complete(600), options={"small_max_degree": 1, "medium_max_degree": 256})
+    res = _check(gcpkg, gg.complete(200), options={"small_max_degree": 1, "medium_max_degree": 256})
 
 
 def test_n_zero(gcpkg):
@@ -168,8 +170,8 @@ def test_validation_rejects_bad_graphs(gcpkg):
 
 def test_invalid_arguments(gcpkg):
     g = gg.gnm(50, 100, 1)
-    for opts in [{"thread_max_degree": 64}, {"block_threads": 96}, {"loop_mode": 3},
-                 {"color_bits": 8}, {"warp_max_degree": 3, "thread_max_degree": 10}]:
+    for opts in [{"small_max_degree": 33}, {"medium_max_degree": 257}, {"block_threads": 96},
+                 {"loop_mode": 3}, {"color_bits": 8}, {"medium_max_degree": 3, "small_max_degree": 10}]:
         res = gcpkg.color(_dev(g.rowptr), _dev(g.colidx), options=opts, check=False)
         assert res.status == gcpkg.GC_ERR_INVALID
 
