@@ -133,9 +133,9 @@ Layout make_layout(int64_t n, size_t elem, const Stats& hs, int64_t round_cap) {
     L.hubs = take((size_t)hs.bin_count[gc::kBinH] * sizeof(gc::HubRecord));
     L.defer = take((size_t)hs.defer * sizeof(int32_t));
     for (int b = 0; b < 2; ++b) {
-        L.S[b] = take((size_t)hs.bin_count[gc::kBinS] * sizeof(int32_t));
-        L.M[b] = take((size_t)hs.bin_count[gc::kBinM] * sizeof(int32_t));
-        L.H[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int32_t));
+        L.S[b] = take((size_t)hs.bin_count[gc::kBinS] * sizeof(int4));
+        L.M[b] = take((size_t)hs.bin_count[gc::kBinM] * sizeof(int4));
+        L.H[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int4));
         L.Hc[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int32_t));
         L.O[b] = take((size_t)hs.hub_chunks * sizeof(int32_t));
     }
@@ -198,7 +198,7 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
                                     cudaMemcpyHostToDevice, s));
         }
         GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 4 * sizeof(unsigned), s));
-        const int64_t tasks = (int64_t)nHC + nM + (nS + 7) / 8;
+        const int64_t tasks = (int64_t)nHC + (nM + 31) / 32 + (nS + 31) / 32;
         const int64_t warps_per_block = threads / 32;
         const int grid = (int)std::max<int64_t>(
             1, std::min<int64_t>((tasks + warps_per_block - 1) / warps_per_block, (int64_t)dc.sms * 8));
@@ -345,14 +345,14 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
         p.X0 = (T*)(base + L.x0);
         p.X1 = (T*)(base + L.x1);
         p.colors_out = colors_out;
-        p.SA = (int32_t*)(base + L.S[0]);
-        p.MA = (int32_t*)(base + L.M[0]);
-        p.HA = (int32_t*)(base + L.H[0]);
+        p.SA = (int4*)(base + L.S[0]);
+        p.MA = (int4*)(base + L.M[0]);
+        p.HA = (int4*)(base + L.H[0]);
         p.HcA = (int32_t*)(base + L.Hc[0]);
         p.OA = (int32_t*)(base + L.O[0]);
-        p.SB = (int32_t*)(base + L.S[1]);
-        p.MB = (int32_t*)(base + L.M[1]);
-        p.HB = (int32_t*)(base + L.H[1]);
+        p.SB = (int4*)(base + L.S[1]);
+        p.MB = (int4*)(base + L.M[1]);
+        p.HB = (int4*)(base + L.H[1]);
         p.HcB = (int32_t*)(base + L.Hc[1]);
         p.OB = (int32_t*)(base + L.O[1]);
         p.defer = (int32_t*)(base + L.defer);

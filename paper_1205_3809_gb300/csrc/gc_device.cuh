@@ -17,10 +17,9 @@
 // pass 1 needs no color reads: v conflicts iff some neighbour precedes it,
 // and then its round-2 color is 2.
 //
-// Work is split into warp-sized tasks with at most 8 adjacency entries per
-// lane, all loads of a task issued before any is used:
-//   S bin (degree <= s_max <= 32): 4 lanes per vertex, 8 vertices per task;
-//   M bin (s_max < degree <= m_max <= 256): one vertex per task;
+// Work is split into warp-sized tasks:
+//   S bin (degree <= s_max <= 32) and M bin (s_max < degree <= m_max <= 256):
+//     32 worklist entries per task, their rows walked as one flat range;
 //   H bin (degree > m_max): one 256-entry chunk of one vertex per task; the
 //     chunks of a vertex OR their conflict flag and color window into a
 //     per-vertex record, and the warp that finishes the last chunk decides.
@@ -37,8 +36,7 @@ namespace gc {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBinS = 0, kBinM = 1, kBinH = 2;
 constexpr int kPerLane = 8;            // adjacency entries per lane and task
-constexpr int kGroup = 4;              // lanes per S-bin vertex
-constexpr int kSmallMaxLimit = kGroup * kPerLane;  // 32
+constexpr int kSmallMaxLimit = 32;    // S bin: degree <= 32
 constexpr int kMedMaxLimit = 32 * kPerLane;        // 256
 constexpr int kChunk = 32 * kPerLane;              // 256 entries per H-bin task
 constexpr int kPass1Flat = 256;        // pass 1: larger degrees take the early-exit path
@@ -62,15 +60,17 @@ struct Stats {
     unsigned long long hub_chunks;  // sum over the H bin of ceil(degree / kChunk)
 };
 
+// The append counters, the two barrier words and the result words sit on
+// separate 128-byte lines, so that blocks polling the barrier do not slow
+// down the atomics of blocks still working.
 struct RoundState {
     unsigned cnt[3][4];    // [k % 3] = {|U_k in S|, |U_k in M|, |U_k in H|, chunks of U_k in H}
     unsigned defer_cnt;    // pass 1: vertices above kPass1Flat
-    unsigned bar_count;
-    unsigned bar_gen;
-    int status;
+    alignas(128) unsigned bar_count;
+    alignas(128) unsigned bar_gen;
+    alignas(128) int status;
     int rounds;
     int max_color;
-    int pad[2];
 };
 
 // Per H-bin vertex of the current round (indexed by its worklist position).
@@ -92,10 +92,11 @@ struct Params {
     T* X0;
     T* X1;
     int32_t* colors_out;
-    // worklists per parity (A: even k, B: odd k): S, M, H vertices,
-    // first chunk of each H vertex, owner position of each chunk
-    int32_t* SA; int32_t* MA; int32_t* HA; int32_t* HcA; int32_t* OA;
-    int32_t* SB; int32_t* MB; int32_t* HB; int32_t* HcB; int32_t* OB;
+    // worklists per parity (A: even k, B: odd k): S, M, H entries
+    // {vertex, row start, degree, 0}, first chunk of each H entry, owner
+    // position of each chunk
+    int4* SA; int4* MA; int4* HA; int32_t* HcA; int32_t* OA;
+    int4* SB; int4* MB; int4* HB; int32_t* HcB; int32_t* OB;
     int32_t* defer;                     // pass 1 early-exit list
     HubRecord* hubs;
     RoundState* st;
@@ -108,6 +109,39 @@ struct Params {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// L2 eviction policies: the adjacency is streamed once per round and should
+// not push the color arrays (gathered at random) out of L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Adjacency entry: read-only for the whole call, streamed.
+__device__ __forceinline__ int32_t ld_adj(const int32_t* a, uint64_t pol) {
+    int32_t r;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return r;
+}
+
+// Color state: written by other blocks in earlier rounds of the same launch,
+// so it is read at L2 (.cg), where it is kept (evict_last).
+__device__ __forceinline__ uint16_t ld_color(const uint16_t* a, uint64_t pol) {
+    uint16_t r;
+    asm volatile("ld.global.cg.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ int32_t ld_color(const int32_t* a, uint64_t pol) {
+    int32_t r;
+    asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return r;
+}
+
 // w precedes v: (prio[w], w) < (prio[v], v); pv = prio[v] (ignored if no prio).
 __device__ __forceinline__ bool precedes(const uint32_t* __restrict__ prio, int32_t w, int32_t v,
                                          uint32_t pv) {
@@ -118,8 +152,19 @@ __device__ __forceinline__ bool precedes(const uint32_t* __restrict__ prio, int3
     return w < v;
 }
 
-// Append v (if flag) to list with one atomic per warp.  All 32 lanes call it.
-__device__ __forceinline__ void warp_append(bool flag, int32_t v, int32_t* list, unsigned* cnt) {
+// Append a worklist entry (if flag) with one atomic per warp.  All lanes call it.
+__device__ __forceinline__ void warp_append(bool flag, int4 e, int4* list, unsigned* cnt) {
+    const unsigned ballot = __ballot_sync(kFull, flag);
+    if (ballot == 0) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(ballot) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(cnt, (unsigned)__popc(ballot));
+    base = __shfl_sync(kFull, base, leader);
+    if (flag) list[base + __popc(ballot & ((1u << lane) - 1u))] = e;
+}
+
+__device__ __forceinline__ void warp_append_i32(bool flag, int32_t v, int32_t* list, unsigned* cnt) {
     const unsigned ballot = __ballot_sync(kFull, flag);
     if (ballot == 0) return;
     const unsigned lane = lane_id();
@@ -132,19 +177,19 @@ __device__ __forceinline__ void warp_append(bool flag, int32_t v, int32_t* list,
 
 // Where the next round's worklists go.
 struct NextLists {
-    int32_t* S; int32_t* M; int32_t* H; int32_t* Hc; int32_t* O;
+    int4* S; int4* M; int4* H; int32_t* Hc; int32_t* O;
     unsigned* cnt;  // {S, M, H, H chunks} of the next round
 };
 
-// Append H-bin vertex v (degree d) to the next round and hand it its chunks.
-// Called by all lanes of a warp; lane `who` holds the vertex.
-__device__ __forceinline__ void warp_append_hub(const NextLists& nl, int32_t v, int32_t d) {
-    const unsigned nch = (unsigned)(d + kChunk - 1) / kChunk;
+// Append H-bin entry e (lane 0's copy) to the next round and hand it its
+// chunks.  Called by all lanes of a warp.
+__device__ __forceinline__ void warp_append_hub(const NextLists& nl, int4 e) {
+    const unsigned nch = (unsigned)(e.z + kChunk - 1) / kChunk;
     unsigned pos = 0, c0 = 0;
     if (lane_id() == 0) {
         pos = atomicAdd(&nl.cnt[kBinH], 1u);
         c0 = atomicAdd(&nl.cnt[3], nch);
-        nl.H[pos] = v;
+        nl.H[pos] = e;
         nl.Hc[pos] = (int32_t)c0;
     }
     pos = __shfl_sync(kFull, pos, 0);
@@ -241,9 +286,10 @@ __device__ __forceinline__ bool grid_barrier(RoundState* st) {
             atomicAdd(&st->bar_gen, 1u);
         } else {
             const unsigned long long t0 = globaltimer_ns();
-            unsigned polls = 0;
+            unsigned polls = 0, nap = 32;
             while (*vgen == gen) {
-                __nanosleep(32);
+                __nanosleep(nap);
+                nap = nap < 256 ? nap * 2 : 256;
                 if (++polls >= kBarrierMaxPolls || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
                     atomicExch(&st->status, kStatusTimeout);
                     ok = 0;
@@ -352,6 +398,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ntasks = ((int64_t)p.n + 31) / 32;
     const NextLists nl = pass1_next(p);
+    const uint64_t pol_adj = policy_evict_first();
     int maxc = 0;
     unsigned vol = 0;
     for (int64_t t = gw; t < ntasks; t += W) {
@@ -388,7 +435,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
                 own[u] = lo;
                 const int32_t ob = __shfl_sync(kFull, b, lo);
                 const int32_t oo = __shfl_sync(kFull, off, lo);
-                w[u] = f < D ? __ldg(p.colidx + ob + (f - oo)) : 0;
+                w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), pol_adj) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -410,16 +457,18 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
         }
         const int bin = bin_of(d, p.s_max, p.m_max);
         const bool go = valid && !defer && hit;
-        warp_append(go && bin == kBinS, v, nl.S, &nl.cnt[kBinS]);
-        warp_append(go && bin == kBinM, v, nl.M, &nl.cnt[kBinM]);
+        const int4 e = make_int4(v, b, d, -1);
+        warp_append(go && bin == kBinS, e, nl.S, &nl.cnt[kBinS]);
+        warp_append(go && bin == kBinM, e, nl.M, &nl.cnt[kBinM]);
         // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
         unsigned hubs = __ballot_sync(kFull, go && bin == kBinH);
         while (hubs) {
             const int j = __ffs(hubs) - 1;
             hubs &= hubs - 1;
-            warp_append_hub(nl, __shfl_sync(kFull, v, j), __shfl_sync(kFull, d, j));
+            warp_append_hub(nl, make_int4(__shfl_sync(kFull, v, j), __shfl_sync(kFull, b, j),
+                                          __shfl_sync(kFull, d, j), -1));
         }
-        warp_append(valid && defer, v, p.defer, &p.st->defer_cnt);
+        warp_append_i32(valid && defer, v, p.defer, &p.st->defer_cnt);
     }
     fold_max_color(p.st, maxc);
     fold_volume(p.round_vol, p.round_cap, 2, vol);
@@ -434,6 +483,7 @@ __global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned nd = __ldcg(&p.st->defer_cnt);
     const NextLists nl = pass1_next(p);
+    const uint64_t pol_adj = policy_evict_first();
     int maxc = 0;
     unsigned vol = 0;
     for (int64_t t = gw; t < nd; t += W) {
@@ -446,7 +496,7 @@ __global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int32_t i = c + 32 * u + (int32_t)lane;
-                w[u] = i < e ? __ldg(p.colidx + i) : -1;
+                w[u] = i < e ? ld_adj(p.colidx + i, pol_adj) : -1;
             }
             bool h = false;
 #pragma unroll
@@ -456,12 +506,13 @@ __global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
         if (lane == 0) pass1_write(p, v, conflict, maxc);
         if (conflict) {
             const int bin = bin_of(e - b, p.s_max, p.m_max);
+            const int4 en = make_int4(v, b, e - b, -1);
             if (lane == 0) vol += (unsigned)(e - b);
             if (bin == kBinH) {
-                warp_append_hub(nl, v, e - b);
+                warp_append_hub(nl, en);
             } else if (lane == 0) {
-                int32_t* list = bin == kBinM ? nl.M : nl.S;
-                list[atomicAdd(&nl.cnt[bin], 1u)] = v;
+                int4* list = bin == kBinM ? nl.M : nl.S;
+                list[atomicAdd(&nl.cnt[bin], 1u)] = en;
             }
         }
     }
@@ -475,8 +526,9 @@ template <typename T>
 struct PassIO {
     const T* Xc;        // C_k
     T* Xn;              // receives C_{k+1} (conflicting) or the final color (settled)
-    const int32_t* S; const int32_t* M; const int32_t* H; const int32_t* Hc; const int32_t* O;
+    const int4* S; const int4* M; const int4* H; const int32_t* Hc; const int32_t* O;
     NextLists next;
+    uint64_t pol_adj, pol_col;
 };
 
 template <typename T>
@@ -496,6 +548,8 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     io.next.Hc = odd ? p.HcA : p.HcB;
     io.next.O = odd ? p.OA : p.OB;
     io.next.cnt = p.st->cnt[(k + 1) % 3];
+    io.pol_adj = policy_evict_first();
+    io.pol_col = policy_evict_last();
     return io;
 }
 
@@ -505,118 +559,154 @@ __device__ __forceinline__ void settle(const Params<T>& p, const PassIO<T>& io, 
     p.colors_out[v] = (int32_t)cv;
 }
 
-// S bin: 8 vertices per task, 4 lanes per vertex, <= 8 entries per lane.
-// First fit <= degree + 1 <= 33, so bits 0..62 of one 64-bit word hold every
-// color that matters; bit 63 carries the conflict flag through the reduction.
+// What a warp needs to start a task: its worklist entry and, for an H-bin
+// chunk, the chunk's first entry.  Loaded one task ahead.
+struct TaskHead {
+    int4 e;      // {vertex, row start, degree, 0}; x < 0 marks an empty S slot
+    int32_t lo;  // H chunk: first adjacency entry of the chunk
+};
+
 template <typename T>
-__device__ __forceinline__ void small_group(const Params<T>& p, const PassIO<T>& io, unsigned t,
-                                            unsigned nS, int& maxc, unsigned& vol) {
-    const unsigned lane = lane_id();
-    const unsigned q = lane & (kGroup - 1);
-    const unsigned i = t * (32 / kGroup) + (lane / kGroup);
-    const bool valid = i < nS;
-    const int32_t v = valid ? __ldcg(io.S + i) : 0;
-    const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
-    const int32_t e = valid ? __ldg(p.rowptr + v + 1) : 0;
-    const T cv = valid ? __ldcg(io.Xc + v) : (T)0;
-    const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
-    int32_t w[kPerLane];
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        const int32_t j = b + (int32_t)q + kGroup * u;
-        w[u] = j < e ? __ldg(p.colidx + j) : -1;
+__device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, unsigned nS,
+                                              unsigned nM, unsigned nHC, unsigned tM) {
+    TaskHead h;
+    h.lo = 0;
+    if (t < nHC) {
+        const int32_t pos = __ldcg(io.O + t);
+        h.e = __ldcg(io.H + pos);
+        h.lo = h.e.y + ((int32_t)t - __ldcg(io.Hc + pos)) * kChunk;
+        h.e.w = pos;
+    } else if (t - nHC < tM) {
+        const unsigned i = (t - nHC) * 32 + lane_id();
+        h.e = i < nM ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
+    } else {
+        const unsigned i = (t - nHC - tM) * 32 + lane_id();
+        h.e = i < nS ? __ldcg(io.S + i) : make_int4(-1, 0, 0, 0);
     }
-    T c[kPerLane];
+    return h;
+}
+
+// S and M bins: 32 worklist entries per task, one per lane.  Their rows are
+// walked as one flat range in batches of 32 entries (lane l of batch u takes
+// flat entry F0 + 32u + l and finds its row by binary search over the rows'
+// running totals), so every lane has an entry in every batch whatever the
+// degrees are.  Each entry ORs its neighbour's color into its row's 256-bit
+// window in shared memory and flags a conflict; afterwards each lane decides
+// its own vertex.  First fit <= degree + 1 <= 257, so only a row of degree
+// 256 can find the window full, and then it rescans.
+constexpr int kFlatBatches = 4;       // batches whose loads are in flight together
+constexpr int kWarpsPerBlockMax = 8;  // block_threads <= 256
+
+template <typename T>
+__device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en, int bin,
+                                          uint32_t* smask, uint32_t* sconf, int& maxc,
+                                          unsigned& vol) {
+    const unsigned lane = lane_id();
+    const bool valid = en.x >= 0;
+    const int32_t v = valid ? en.x : 0;
+    const int32_t b = en.y;
+    const int32_t d = valid ? en.z : 0;
+    const T cv = valid ? ld_color(io.Xc + v, io.pol_col) : (T)0;
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
-    uint64_t mask = 0;
+    for (int q = 0; q < 8; ++q) smask[lane * 8 + q] = 0u;
+    if (lane == 0) *sconf = 0u;
+    int32_t incl = d;
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        if (w[u] >= 0) {
-            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) mask |= 1ull << 63;
-            const unsigned idx = (unsigned)c[u] - 1u;
-            mask |= idx < 63u ? (1ull << idx) : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t x = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += x;
+    }
+    const int32_t off = incl - d;
+    const int32_t D = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    for (int32_t F0 = 0; F0 < D; F0 += 32 * kFlatBatches) {
+        int32_t w[kFlatBatches], own[kFlatBatches];
+#pragma unroll
+        for (int u = 0; u < kFlatBatches; ++u) {
+            const int32_t f = F0 + 32 * u + (int32_t)lane;
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int mid = (lo + hi) >> 1;
+                const int32_t val = __shfl_sync(kFull, incl, mid);
+                if (val > f) hi = mid; else lo = mid + 1;
+            }
+            own[u] = lo;
+            const int32_t ob = __shfl_sync(kFull, b, lo);
+            const int32_t oo = __shfl_sync(kFull, off, lo);
+            w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), io.pol_adj) : -1;
+        }
+        T c[kFlatBatches];
+#pragma unroll
+        for (int u = 0; u < kFlatBatches; ++u)
+            c[u] = w[u] >= 0 ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+#pragma unroll
+        for (int u = 0; u < kFlatBatches; ++u) {
+            const T ocv = __shfl_sync(kFull, cv, own[u]);
+            const int32_t ov = __shfl_sync(kFull, v, own[u]);
+            if (w[u] >= 0) {
+                if (c[u] == ocv &&
+                    precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u))
+                    atomicOr(sconf, 1u << own[u]);
+                const unsigned idx = (unsigned)c[u] - 1u;
+                if (idx < 256u) atomicOr(&smask[own[u] * 8 + (idx >> 5)], 1u << (idx & 31u));
+            }
         }
     }
-    mask |= __shfl_xor_sync(kFull, mask, 1);
-    mask |= __shfl_xor_sync(kFull, mask, 2);
-    const bool conflict = valid && (mask >> 63) != 0;
-    if (valid && q == 0) {
+    __syncwarp();
+    const bool conflict = valid && ((*sconf >> lane) & 1u);
+    unsigned color = 0;
+    bool rescan = false;
+    if (conflict) {
+        int ff = -1;
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            const uint32_t word = smask[lane * 8 + q];
+            if (word != 0xffffffffu) ff = q * 32 + __ffs(~word) - 1;
+        }
+        if (ff >= 0) color = (unsigned)ff + 1u;
+        else rescan = true;
+    }
+    unsigned need = __ballot_sync(kFull, rescan);
+    while (need) {
+        const int j = __ffs(need) - 1;
+        need &= need - 1;
+        const int32_t jb = __shfl_sync(kFull, b, j), jd = __shfl_sync(kFull, d, j);
+        const unsigned cj = rescan_first_fit(p.colidx, io.Xc, jb, jb + jd);
+        if ((int)lane == j) color = cj;
+    }
+    if (valid) {
         if (conflict) {
-            io.Xn[v] = (T)__ffsll((long long)~mask);
-            vol += (unsigned)(e - b);
+            io.Xn[v] = (T)color;
+            vol += (unsigned)d;
         } else {
             settle(p, io, v, cv);
             maxc = max(maxc, (int)cv);
         }
     }
-    warp_append(conflict && q == 0, v, io.next.S, &io.next.cnt[kBinS]);
+    warp_append(conflict, en, bin == kBinS ? io.next.S : io.next.M, &io.next.cnt[bin]);
+    __syncwarp();
 }
 
-// M bin: one vertex per task, <= 8 entries per lane.
+// H bin: one 256-entry chunk of the vertex at worklist position en.w.  The
+// warp that completes the vertex's last chunk decides it and clears its record.
 template <typename T>
-__device__ __forceinline__ void medium_vertex(const Params<T>& p, const PassIO<T>& io, int32_t v,
-                                              int& maxc, unsigned& vol) {
-    const unsigned lane = lane_id();
-    const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-    const T cv = __ldcg(io.Xc + v);
-    const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-    int32_t w[kPerLane];
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        const int32_t j = b + (int32_t)lane + 32 * u;
-        w[u] = j < e ? __ldg(p.colidx + j) : -1;
-    }
-    T c[kPerLane];
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
-    bool conflict = false;
-    Mask256 m;
-    m.clear();
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        if (w[u] >= 0) {
-            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
-            m.set((unsigned)c[u] - 1u);
-        }
-    }
-    if (!__any_sync(kFull, conflict)) {
-        if (lane == 0) settle(p, io, v, cv);
-        maxc = max(maxc, (int)cv);
-        return;
-    }
-    int ff = window_first_clear(m.warp_reduce_word());
-    const unsigned color = ff >= 0 ? (unsigned)ff + 1u : rescan_first_fit(p.colidx, io.Xc, b, e);
-    if (lane == 0) {
-        io.Xn[v] = (T)color;
-        io.next.M[atomicAdd(&io.next.cnt[kBinM], 1u)] = v;
-        vol += (unsigned)(e - b);
-    }
-}
-
-// H bin: chunk t of the vertex at worklist position O[t].  The warp that
-// completes the vertex's last chunk decides it and clears its record.
-template <typename T>
-__device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, unsigned t,
+__device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
                                           int& maxc, unsigned& vol) {
     const unsigned lane = lane_id();
-    const int32_t pos = __ldcg(io.O + t);
-    const int32_t v = __ldcg(io.H + pos);
-    const int32_t c0 = __ldcg(io.Hc + pos);
-    const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-    const int32_t lo = b + ((int32_t)t - c0) * kChunk;
-    const int32_t hi = min(e, lo + kChunk);
-    const T cv = __ldcg(io.Xc + v);
-    const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
+    const int32_t v = h.e.x, b = h.e.y, e = h.e.y + h.e.z, pos = h.e.w;
+    const int32_t lo = h.lo, hi = min(e, lo + kChunk);
     int32_t w[kPerLane];
 #pragma unroll
     for (int u = 0; u < kPerLane; ++u) {
         const int32_t j = lo + (int32_t)lane + 32 * u;
-        w[u] = j < hi ? __ldg(p.colidx + j) : -1;
+        w[u] = j < hi ? ld_adj(p.colidx + j, io.pol_adj) : -1;
     }
+    const T cv = ld_color(io.Xc + v, io.pol_col);
     T c[kPerLane];
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? __ldcg(io.Xc + w[u]) : (T)0;
+    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+    const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
     bool conflict = false;
     Mask256 m;
     m.clear();
@@ -654,28 +744,36 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
         io.Xn[v] = (T)color;
         vol += (unsigned)(e - b);
     }
-    warp_append_hub(io.next, v, e - b);
+    warp_append_hub(io.next, make_int4(v, b, e - b, -1));
 }
 
 // One fused pass over U_k.  Task t: first the H-bin chunks, then the M-bin
-// vertices, then groups of 8 S-bin vertices; warp w takes t = w, w + W, ...
+// and S-bin entries 32 at a time; warp w takes t = w, w + W, ... and loads
+// the head of its next task before working on the current one.
 template <typename T>
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc) {
+    __shared__ uint32_t s_mask[kWarpsPerBlockMax][32 * 8];
+    __shared__ uint32_t s_conf[kWarpsPerBlockMax];
     const PassIO<T> io = pass_io(p, k);
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned W = (gridDim.x * blockDim.x) >> 5;
-    const unsigned groups = (nS + (32 / kGroup) - 1) / (32 / kGroup);
-    const unsigned total = nHC + nM + groups;
+    const unsigned wib = threadIdx.x >> 5;
+    const unsigned tM = (nM + 31) / 32, tS = (nS + 31) / 32;
+    const unsigned total = nHC + tM + tS;
     unsigned vol = 0;  // this lane's share of vol(U_{k+1})
+    TaskHead cur;
+    if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM);
     for (unsigned t = gw; t < total; t += W) {
+        const unsigned tn = t + W;
+        TaskHead nxt;
+        if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM);
         if (t < nHC) {
-            hub_chunk(p, io, t, maxc, vol);
-        } else if (t - nHC < nM) {
-            medium_vertex(p, io, __ldcg(io.M + (t - nHC)), maxc, vol);
+            hub_chunk(p, io, cur, maxc, vol);
         } else {
-            small_group(p, io, t - nHC - nM, nS, maxc, vol);
+            flat_task(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_mask[wib], &s_conf[wib], maxc, vol);
         }
+        cur = nxt;
     }
     fold_volume(p.round_vol, p.round_cap, k + 1, vol);
 }
@@ -684,7 +782,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
 // separates the rounds.  Every block reads the same counts after a barrier,
 // so all blocks leave the loop in the same round.
 template <typename T>
-__global__ void __launch_bounds__(256) rounds_persistent_kernel(Params<T> p) {
+__global__ void __launch_bounds__(256, 5) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
     for (int k = 2;; ++k) {
@@ -716,7 +814,7 @@ __global__ void __launch_bounds__(256) rounds_persistent_kernel(Params<T> p) {
 
 // One pass per launch (loop mode 1): counts come from the host.
 template <typename T>
-__global__ void __launch_bounds__(256) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
+__global__ void __launch_bounds__(256, 5) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
                                                     unsigned nHC) {
     int maxc = 0;
     run_pass(p, k, nS, nM, nHC, maxc);
