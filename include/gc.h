@@ -72,13 +72,17 @@ typedef struct gc_options {
     int32_t loop_mode;         /* 0: all rounds in one persistent cooperative
                                   launch (default); 1: one launch per round,
                                   the host reads |U| after each */
-    int32_t color_bits;        /* 0: automatic (16-bit color state when the
-                                  maximum degree is below 65535, else 32);
-                                  16 or 32 to force one */
+    int32_t color_bits;        /* 0 or 16: 16-bit color state (a flag bit and
+                                  colors below 2^15), and if a color does not
+                                  fit, the call starts over with 32-bit state;
+                                  32: 32-bit state from the start */
     int32_t block_threads;     /* threads per block: 128 or 256 (default) */
     int32_t telemetry;         /* 1: time the phases with CUDA events on the
                                   call's stream (see gc_last_phase_ms) */
-    int32_t reserved[8];
+    int32_t narrow_color_limit; /* testing: with 16-bit state, treat colors >=
+                                  this as not fitting (0: 2^15), to exercise
+                                  the 32-bit restart */
+    int32_t reserved[7];
 } gc_options;
 
 /*

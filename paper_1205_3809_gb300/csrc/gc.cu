@@ -111,17 +111,17 @@ int ensure_host(void** p, size_t* have, size_t need) {
 }
 
 struct Layout {
-    size_t st, stats, rs, rv, x0, x1, hubs, defer;
+    size_t st, stats, rs, rv, x0, x1, act0, act1, stat, hubs, defer;
     size_t S[2], M[2], H[2], Hc[2], O[2];
     size_t total;
 };
 
-Layout make_layout(int64_t n, size_t elem, const Stats& hs, int64_t round_cap) {
+Layout make_layout(int64_t n, int64_t nnz, size_t elem, const Stats& hs, int64_t round_cap) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
-        off = align_up(off + std::max<size_t>(bytes, 4), 256);
+        off = align_up(off + std::max<size_t>(bytes, 16), 256);
         return o;
     };
     L.st = take(sizeof(RoundState));
@@ -130,13 +130,16 @@ Layout make_layout(int64_t n, size_t elem, const Stats& hs, int64_t round_cap) {
     L.rv = take((size_t)round_cap * sizeof(unsigned long long));
     L.x0 = take((size_t)n * elem);
     L.x1 = take((size_t)n * elem);
-    L.hubs = take((size_t)hs.bin_count[gc::kBinH] * sizeof(gc::HubRecord));
+    L.act0 = take((size_t)nnz * sizeof(int32_t));
+    L.act1 = take((size_t)nnz * sizeof(int32_t));
+    L.stat = take((size_t)n * 8 * sizeof(uint32_t));
+    L.hubs = take((size_t)hs.cap[gc::kBinH] * sizeof(gc::HubRecord));
     L.defer = take((size_t)hs.defer * sizeof(int32_t));
     for (int b = 0; b < 2; ++b) {
-        L.S[b] = take((size_t)hs.bin_count[gc::kBinS] * sizeof(int4));
-        L.M[b] = take((size_t)hs.bin_count[gc::kBinM] * sizeof(int4));
-        L.H[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int4));
-        L.Hc[b] = take((size_t)hs.bin_count[gc::kBinH] * sizeof(int32_t));
+        L.S[b] = take((size_t)hs.cap[gc::kBinS] * sizeof(int4));
+        L.M[b] = take((size_t)hs.cap[gc::kBinM] * sizeof(int4));
+        L.H[b] = take((size_t)hs.cap[gc::kBinH] * sizeof(int4));
+        L.Hc[b] = take((size_t)hs.cap[gc::kBinH] * sizeof(int32_t));
         L.O[b] = take((size_t)hs.hub_chunks * sizeof(int32_t));
     }
     L.total = off;
@@ -152,7 +155,7 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)dc.sms * 8));
         gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
-        gc::pass1_defer_kernel<T><<<dc.sms * 2, 256, 0, s>>>(p);
+        gc::pass1_long_kernel<T><<<dc.sms * 2, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
         *launches += 2;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
@@ -218,6 +221,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->small_max_degree == 0) o->small_max_degree = gc::kSmallMaxLimit;
     if (o->medium_max_degree == 0) o->medium_max_degree = gc::kMedMaxLimit;
     if (o->block_threads == 0) o->block_threads = 256;
+    if (o->narrow_color_limit < 0) return GC_ERR_INVALID;
     if (o->small_max_degree < 1 || o->small_max_degree > gc::kSmallMaxLimit) return GC_ERR_INVALID;
     if (o->medium_max_degree < o->small_max_degree || o->medium_max_degree > gc::kMedMaxLimit)
         return GC_ERR_INVALID;
@@ -317,61 +321,77 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     std::memcpy(&hs, dc.host, sizeof(Stats));
     if (hs.bad || hs.nnz < 0) return GC_ERR_BAD_GRAPH;
     if (hs.nnz > 0 && !colidx) return GC_ERR_INVALID;
-    int bits = o.color_bits;
-    if (bits == 0) bits = (hs.max_degree + 1 <= 65535) ? 16 : 32;
-    if (bits == 16 && hs.max_degree + 1 > 65535) return GC_ERR_INVALID;
-    const size_t elem = bits == 16 ? 2 : 4;
+    // 16-bit color words (flag + 15-bit color) unless asked for 32; a color
+    // that does not fit makes the rounds stop with an overflow status, and the
+    // call starts over with 32-bit words.
+    int bits = o.color_bits == 32 ? 32 : 16;
+    Layout L;
+    char* base = nullptr;
+    RoundState* st = nullptr;
+    for (;;) {
+        const size_t elem = bits == 16 ? 2 : 4;
+        L = make_layout(n, hs.nnz, elem, hs, round_cap);
+        rc = ensure_device(&dc.ws, &dc.ws_bytes, L.total);
+        if (rc != GC_OK) return rc;
+        base = (char*)dc.ws;
+        st = (RoundState*)(base + L.st);
+        GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
+        GC_CUDA(cudaMemsetAsync(base + L.rv, 0, (size_t)round_cap * sizeof(unsigned long long), s));
+        GC_CUDA(cudaMemsetAsync(base + L.hubs, 0, (size_t)hs.cap[gc::kBinH] * sizeof(gc::HubRecord), s));
 
-    // 2. workspace
-    const Layout L = make_layout(n, elem, hs, round_cap);
-    rc = ensure_device(&dc.ws, &dc.ws_bytes, L.total);
-    if (rc != GC_OK) return rc;
-    char* base = (char*)dc.ws;
-    RoundState* st = (RoundState*)(base + L.st);
-    GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
-    GC_CUDA(cudaMemsetAsync(base + L.rv, 0, (size_t)round_cap * sizeof(unsigned long long), s));
-    GC_CUDA(cudaMemsetAsync(base + L.hubs, 0, (size_t)hs.bin_count[gc::kBinH] * sizeof(gc::HubRecord), s));
-
-    auto fill = [&](auto& p) {
-        using PT = std::remove_reference_t<decltype(p)>;
-        using T = std::remove_pointer_t<decltype(PT::X0)>;
-        p.rowptr = rowptr;
-        p.colidx = colidx;
-        p.prio = priority;
-        p.n = n;
-        p.s_max = o.small_max_degree;
-        p.m_max = o.medium_max_degree;
-        p.max_rounds = max_rounds;
-        p.X0 = (T*)(base + L.x0);
-        p.X1 = (T*)(base + L.x1);
-        p.colors_out = colors_out;
-        p.SA = (int4*)(base + L.S[0]);
-        p.MA = (int4*)(base + L.M[0]);
-        p.HA = (int4*)(base + L.H[0]);
-        p.HcA = (int32_t*)(base + L.Hc[0]);
-        p.OA = (int32_t*)(base + L.O[0]);
-        p.SB = (int4*)(base + L.S[1]);
-        p.MB = (int4*)(base + L.M[1]);
-        p.HB = (int4*)(base + L.H[1]);
-        p.HcB = (int32_t*)(base + L.Hc[1]);
-        p.OB = (int32_t*)(base + L.O[1]);
-        p.defer = (int32_t*)(base + L.defer);
-        p.hubs = (gc::HubRecord*)(base + L.hubs);
-        p.st = st;
-        p.round_sizes = (int32_t*)(base + L.rs);
-        p.round_vol = (unsigned long long*)(base + L.rv);
-        p.round_cap = (int32_t)round_cap;
-    };
-    if (bits == 16) {
-        Params<uint16_t> p;
-        fill(p);
-        rc = run_rounds(o, dc, p, s, &launches);
-    } else {
-        Params<int32_t> p;
-        fill(p);
-        rc = run_rounds(o, dc, p, s, &launches);
+        auto fill = [&](auto& p) {
+            using PT = std::remove_reference_t<decltype(p)>;
+            using T = std::remove_pointer_t<decltype(PT::X0)>;
+            p.rowptr = rowptr;
+            p.colidx = colidx;
+            p.prio = priority;
+            p.n = n;
+            p.s_max = o.small_max_degree;
+            p.m_max = o.medium_max_degree;
+            p.max_rounds = max_rounds;
+            p.color_limit = bits == 16 ? (o.narrow_color_limit > 0 ? (uint32_t)o.narrow_color_limit : 0x8000u)
+                                       : 0x80000000u;
+            p.X0 = (T*)(base + L.x0);
+            p.X1 = (T*)(base + L.x1);
+            p.colors_out = colors_out;
+            p.act0 = (int32_t*)(base + L.act0);
+            p.act1 = (int32_t*)(base + L.act1);
+            p.stat = (uint32_t*)(base + L.stat);
+            p.SA = (int4*)(base + L.S[0]);
+            p.MA = (int4*)(base + L.M[0]);
+            p.HA = (int4*)(base + L.H[0]);
+            p.HcA = (int32_t*)(base + L.Hc[0]);
+            p.OA = (int32_t*)(base + L.O[0]);
+            p.SB = (int4*)(base + L.S[1]);
+            p.MB = (int4*)(base + L.M[1]);
+            p.HB = (int4*)(base + L.H[1]);
+            p.HcB = (int32_t*)(base + L.Hc[1]);
+            p.OB = (int32_t*)(base + L.O[1]);
+            p.defer = (int32_t*)(base + L.defer);
+            p.hubs = (gc::HubRecord*)(base + L.hubs);
+            p.st = st;
+            p.round_sizes = (int32_t*)(base + L.rs);
+            p.round_vol = (unsigned long long*)(base + L.rv);
+            p.round_cap = (int32_t)round_cap;
+        };
+        if (bits == 16) {
+            Params<uint16_t> p;
+            fill(p);
+            rc = run_rounds(o, dc, p, s, &launches);
+        } else {
+            Params<int32_t> p;
+            fill(p);
+            rc = run_rounds(o, dc, p, s, &launches);
+        }
+        if (rc != GC_OK) return rc;
+        if (bits == 32) break;
+        int status = 0;
+        GC_CUDA(cudaMemcpyAsync(dc.host, &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(&status, dc.host, sizeof(int));
+        if (status != gc::kStatusColorOverflow) break;
+        bits = 32;
     }
-    if (rc != GC_OK) return rc;
 
     // 4. results
     if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[3], s));

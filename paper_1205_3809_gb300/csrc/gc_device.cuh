@@ -11,21 +11,32 @@
 // two-phase form would read every adjacency twice.
 //
 // Double buffering: pass k reads X[k & 1] and writes X[(k + 1) & 1].  A
-// vertex that settles in pass k writes its final color to the other buffer
-// too, so both buffers hold it from then on; no copy of the whole array is
-// ever needed.  Round 1 colors every vertex 1 (all colors start at 0), so
-// pass 1 needs no color reads: v conflicts iff some neighbour precedes it,
-// and then its round-2 color is 2.
+// vertex that settles writes its final color to both buffers, so no copy of
+// the whole array is ever needed.  Round 1 colors every vertex 1 (all colors
+// start at 0), so pass 1 needs no color reads: v conflicts iff some
+// neighbour precedes it, and then its round-2 color is 2.
 //
-// Work is split into warp-sized tasks:
-//   S bin (degree <= s_max <= 32) and M bin (s_max < degree <= m_max <= 256):
-//     32 worklist entries per task, their rows walked as one flat range;
-//   H bin (degree > m_max): one 256-entry chunk of one vertex per task; the
-//     chunks of a vertex OR their conflict flag and color window into a
-//     per-vertex record, and the warp that finishes the last chunk decides.
+// Active lists.  A color word carries a flag bit once its vertex has settled
+// (its color is final).  A vertex v still in U reads each neighbour's word
+// anyway (the conflict test and first fit need this round's color), and a
+// flagged neighbour is then folded into v's static mask (the colors 1..256
+// held by settled neighbours, kept per vertex across rounds) and dropped
+// from v's active list, which pass k rewrites compacted into the other of
+// two buffers.  Later rounds read only the neighbours that had not settled,
+// plus v's static mask; first fit looks at static | this round's colors.  A
+// first fit beyond 256 rescans the original row (every neighbour).  The
+// flag makes 16-bit state hold colors < 2^15: a larger color sets an
+// overflow status and the host reruns with 32-bit state.
+//
+// Work is split into warp-sized tasks, binned by the current active length:
+//   S bin (length <= s_max <= 32) and M bin (s_max < length <= m_max <= 256):
+//     32 worklist entries per task, their lists walked as one flat range;
+//   H bin (length > m_max): one 256-entry chunk of one list per task; the
+//     chunks of a vertex OR their conflict flag and color windows into a
+//     per-vertex record, write their survivors at offsets taken from an
+//     atomic counter, and the warp that finishes the last chunk decides.
 // Tasks are dealt to warps round-robin; no block-wide barrier is taken
-// inside a round.  A vertex's bin never changes, so a vertex sent back is
-// appended to the worklist of its own bin.
+// inside a round.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,29 +46,46 @@ namespace gc {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBinS = 0, kBinM = 1, kBinH = 2;
-constexpr int kPerLane = 8;            // adjacency entries per lane and task
-constexpr int kSmallMaxLimit = 32;    // S bin: degree <= 32
-constexpr int kMedMaxLimit = 32 * kPerLane;        // 256
-constexpr int kChunk = 32 * kPerLane;              // 256 entries per H-bin task
-constexpr int kPass1Flat = 256;        // pass 1: larger degrees take the early-exit path
+constexpr int kPerLane = 8;                   // adjacency entries per lane in a hub chunk
+constexpr int kSmallMaxLimit = 32;            // S bin: length <= 32
+constexpr int kMedMaxLimit = 32 * kPerLane;   // M bin: length <= 256
+constexpr int kChunk = 32 * kPerLane;         // 256 entries per H-bin task
+constexpr int kPass1Flat = 256;               // pass 1: longer rows take the per-warp path
+constexpr int kFlatBatches = 4;               // flat tasks: batches in flight together
+constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
 
-// Status codes shared with gc.h (kept numerically equal).
+// Status codes shared with gc.h (kept numerically equal), and one internal.
 constexpr int kStatusOk = 0;
 constexpr int kStatusMaxRounds = -4;
 constexpr int kStatusTimeout = -5;
+constexpr int kStatusColorOverflow = -100;    // 16-bit state too narrow: rerun with 32-bit
 
 // A grid barrier gives up after this long (globaltimer ns) or this many polls.
 constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;
 constexpr unsigned kBarrierMaxPolls = 1u << 26;
+
+// Settled flag and color field of a color word.
+template <typename T> struct Word;
+template <> struct Word<uint16_t> { static constexpr uint32_t kFlag = 0x8000u; };
+template <> struct Word<int32_t> { static constexpr uint32_t kFlag = 0x80000000u; };
+
+template <typename T>
+__device__ __forceinline__ uint32_t word_raw(T x) {
+    return sizeof(T) == 2 ? (uint32_t)(uint16_t)x : (uint32_t)x;
+}
+template <typename T>
+__device__ __forceinline__ uint32_t word_color(T x) { return word_raw(x) & (Word<T>::kFlag - 1u); }
+template <typename T>
+__device__ __forceinline__ bool word_settled(T x) { return (word_raw(x) & Word<T>::kFlag) != 0u; }
 
 struct Stats {
     int max_degree;
     int bad;                      // rowptr[0] != 0 or a negative degree
     int nnz;                      // rowptr[n]
     unsigned defer;               // vertices with degree > kPass1Flat
-    unsigned bin_count[3];        // vertices per degree bin
+    unsigned cap[3];              // list capacities: degree >= 1, > s_max, > m_max
     unsigned pad;
-    unsigned long long hub_chunks;  // sum over the H bin of ceil(degree / kChunk)
+    unsigned long long hub_chunks;  // sum over degree > m_max of ceil(degree / kChunk)
 };
 
 // The append counters, the two barrier words and the result words sit on
@@ -75,10 +103,12 @@ struct RoundState {
 
 // Per H-bin vertex of the current round (indexed by its worklist position).
 struct HubRecord {
-    unsigned mask[8];      // colors 1..256 seen by any chunk
+    unsigned mask[8];      // colors 1..256 seen by any chunk this round
+    unsigned stat[8];      // colors 1..256 of neighbours found settled this round
     unsigned conflict;
     unsigned done;         // chunks finished
-    unsigned pad[6];
+    unsigned kept;         // active entries kept for the next round
+    unsigned pad[13];
 };
 
 template <typename T>
@@ -87,21 +117,25 @@ struct Params {
     const int32_t* __restrict__ colidx;
     const uint32_t* __restrict__ prio;  // NULL = index priority
     int32_t n;
-    int32_t s_max, m_max;               // degree bin limits
+    int32_t s_max, m_max;               // length bin limits
     int32_t max_rounds;
+    uint32_t color_limit;               // a color >= this overflows (16-bit state)
     T* X0;
     T* X1;
     int32_t* colors_out;
+    int32_t* act0;                      // active lists (row starts as in colidx)
+    int32_t* act1;
+    uint32_t* stat;                     // static masks, 8 words per vertex
     // worklists per parity (A: even k, B: odd k): S, M, H entries
-    // {vertex, row start, degree, 0}, first chunk of each H entry, owner
-    // position of each chunk
+    // {vertex, row start, active length, degree}, first chunk of each H
+    // entry, owner position of each chunk
     int4* SA; int4* MA; int4* HA; int32_t* HcA; int32_t* OA;
     int4* SB; int4* MB; int4* HB; int32_t* HcB; int32_t* OB;
-    int32_t* defer;                     // pass 1 early-exit list
+    int32_t* defer;                     // pass 1: rows longer than kPass1Flat
     HubRecord* hubs;
     RoundState* st;
     int32_t* round_sizes;               // device telemetry, round_sizes[k-1] = |U_k|
-    unsigned long long* round_vol;      // device telemetry, round_vol[k-1] = vol(U_k)
+    unsigned long long* round_vol;      // device telemetry, round_vol[k-1] = entries round k reads
     int32_t round_cap;
 };
 
@@ -109,8 +143,8 @@ struct Params {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// L2 eviction policies: the adjacency is streamed once per round and should
-// not push the color arrays (gathered at random) out of L2.
+// L2 eviction policies: adjacency is streamed and should not push the color
+// arrays (gathered at random) out of L2.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -122,14 +156,21 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     return pol;
 }
 
-// Adjacency entry: read-only for the whole call, streamed.
+// Adjacency / active-list entry.  colidx is read-only for the whole call;
+// an active list is written in one round and read in the next, within the
+// same launch, so it is read at L2 (.cg).
+__device__ __forceinline__ int32_t ld_row(const int32_t* a, uint64_t pol) {
+    int32_t r;
+    asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return r;
+}
 __device__ __forceinline__ int32_t ld_adj(const int32_t* a, uint64_t pol) {
     int32_t r;
     asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
     return r;
 }
 
-// Color state: written by other blocks in earlier rounds of the same launch,
+// Color word: written by other blocks in earlier rounds of the same launch,
 // so it is read at L2 (.cg), where it is kept (evict_last).
 __device__ __forceinline__ uint16_t ld_color(const uint16_t* a, uint64_t pol) {
     uint16_t r;
@@ -179,7 +220,12 @@ __device__ __forceinline__ void warp_append_i32(bool flag, int32_t v, int32_t* l
 struct NextLists {
     int4* S; int4* M; int4* H; int32_t* Hc; int32_t* O;
     unsigned* cnt;  // {S, M, H, H chunks} of the next round
+    int32_t s_max, m_max;
 };
+
+__device__ __forceinline__ int bin_of(int32_t len, int32_t s_max, int32_t m_max) {
+    return len <= s_max ? kBinS : (len <= m_max ? kBinM : kBinH);
+}
 
 // Append H-bin entry e (lane 0's copy) to the next round and hand it its
 // chunks.  Called by all lanes of a warp.
@@ -195,6 +241,17 @@ __device__ __forceinline__ void warp_append_hub(const NextLists& nl, int4 e) {
     pos = __shfl_sync(kFull, pos, 0);
     c0 = __shfl_sync(kFull, c0, 0);
     for (unsigned j = lane_id(); j < nch; j += 32) nl.O[c0 + j] = (int32_t)pos;
+}
+
+// Append one entry held by lane 0 (any bin).  Called by all lanes of a warp.
+__device__ __forceinline__ void warp_append_one(const NextLists& nl, int4 e) {
+    const int bin = bin_of(e.z, nl.s_max, nl.m_max);
+    if (bin == kBinH) {
+        warp_append_hub(nl, e);
+    } else if (lane_id() == 0) {
+        int4* list = bin == kBinM ? nl.M : nl.S;
+        list[atomicAdd(&nl.cnt[bin], 1u)] = e;
+    }
 }
 
 // Bits of colors base+1 .. base+256 seen by one lane.
@@ -245,17 +302,20 @@ __device__ __forceinline__ int window_first_clear(uint32_t word) {
     return q * 32 + __ffs(~wq) - 1;
 }
 
-// First fit beyond the first window: rescan adj(v) for windows base+1 ..
-// until one has a free color.  Terminates: a full window of 256 colors needs
-// 256 more neighbours, and first fit never exceeds degree + 1.
+// First fit beyond the first window: rescan v's whole original row (settled
+// neighbours were dropped from the active list) for windows base+1 .. until
+// one has a free color.  Terminates: a full window of 256 colors needs 256
+// more neighbours, and first fit never exceeds degree + 1.
 template <typename T>
-__device__ __forceinline__ unsigned rescan_first_fit(const int32_t* __restrict__ colidx, const T* Xc,
-                                                     int32_t b, int32_t e) {
+__device__ __forceinline__ unsigned rescan_first_fit(const int32_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colidx, const T* Xc,
+                                                     int32_t v) {
+    const int32_t b = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
     for (unsigned base = 256u;; base += 256u) {
         Mask256 m;
         m.clear();
         for (int32_t i = b + (int32_t)lane_id(); i < e; i += 32)
-            m.set((unsigned)__ldcg(Xc + __ldg(colidx + i)) - 1u - base);
+            m.set(word_color(__ldcg(Xc + __ldg(colidx + i))) - 1u - base);
         const int ff = window_first_clear(m.warp_reduce_word());
         if (ff >= 0) return base + (unsigned)ff + 1u;
     }
@@ -310,49 +370,44 @@ __device__ __forceinline__ void fold_max_color(RoundState* st, int maxc) {
     if (lane_id() == 0 && m > 0) atomicMax(&st->max_color, m);
 }
 
-// Add a warp's share of vol(U_r) (sum of degrees) to round_vol[r-1].
+// Add a warp's share of the next round's read volume to round_vol[r-1].
 __device__ __forceinline__ void fold_volume(unsigned long long* round_vol, int32_t cap, int r,
                                             unsigned vol) {
     const unsigned s = __reduce_add_sync(kFull, vol);
     if (lane_id() == 0 && s && r - 1 < cap) atomicAdd(&round_vol[r - 1], (unsigned long long)s);
 }
 
-__device__ __forceinline__ int bin_of(int32_t d, int32_t s_max, int32_t m_max) {
-    return d <= s_max ? kBinS : (d <= m_max ? kBinM : kBinH);
-}
-
 // ------------------------------------------------------------ setup scan
 
-// Degree statistics: max degree, vertices per bin, hub chunks, rowptr checks.
+// Degree statistics: max degree, list capacities, hub chunks, rowptr checks.
 __global__ void stats_kernel(const int32_t* __restrict__ rowptr, int32_t n, int32_t s_max,
                              int32_t m_max, Stats* s) {
     int mx = 0, bad = 0;
-    unsigned b0 = 0, b1 = 0, b2 = 0, df = 0;
+    unsigned c0 = 0, c1 = 0, c2 = 0, df = 0;
     unsigned long long ch = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t d = __ldg(rowptr + v + 1) - __ldg(rowptr + v);
         if (d < 0) { bad = 1; continue; }
         mx = max(mx, d);
-        const int bin = bin_of(d, s_max, m_max);
-        b0 += bin == kBinS;
-        b1 += bin == kBinM;
-        b2 += bin == kBinH;
+        c0 += d >= 1;
+        c1 += d > s_max;
+        c2 += d > m_max;
         df += d > kPass1Flat;
-        if (bin == kBinH) ch += (unsigned long long)((d + kChunk - 1) / kChunk);
+        if (d > m_max) ch += (unsigned long long)((d + kChunk - 1) / kChunk);
     }
     mx = __reduce_max_sync(kFull, mx);
     bad = __reduce_or_sync(kFull, (unsigned)bad);
-    b0 = __reduce_add_sync(kFull, b0);
-    b1 = __reduce_add_sync(kFull, b1);
-    b2 = __reduce_add_sync(kFull, b2);
+    c0 = __reduce_add_sync(kFull, c0);
+    c1 = __reduce_add_sync(kFull, c1);
+    c2 = __reduce_add_sync(kFull, c2);
     df = __reduce_add_sync(kFull, df);
     if (lane_id() == 0) {
         atomicMax(&s->max_degree, mx);
         if (bad) s->bad = 1;
-        if (b0) atomicAdd(&s->bin_count[0], b0);
-        if (b1) atomicAdd(&s->bin_count[1], b1);
-        if (b2) atomicAdd(&s->bin_count[2], b2);
+        if (c0) atomicAdd(&s->cap[0], c0);
+        if (c1) atomicAdd(&s->cap[1], c1);
+        if (c2) atomicAdd(&s->cap[2], c2);
         if (df) atomicAdd(&s->defer, df);
     }
     for (int o = 16; o > 0; o >>= 1) ch += __shfl_xor_sync(kFull, ch, o);
@@ -366,12 +421,15 @@ __global__ void stats_kernel(const int32_t* __restrict__ rowptr, int32_t n, int3
 // ------------------------------------------------------------- pass 1
 
 // Outcome of round 1 for v: C_2[v] = 2 if it conflicts (then it joins U_2),
-// else v keeps color 1 for good.
+// else v keeps color 1 for good (flagged in both buffers).
 template <typename T>
 __device__ __forceinline__ void pass1_write(const Params<T>& p, int32_t v, bool conflict, int& maxc) {
-    p.X0[v] = conflict ? (T)2 : (T)1;
-    if (!conflict) {
-        p.X1[v] = (T)1;
+    if (conflict) {
+        p.X0[v] = (T)2;
+    } else {
+        const T one = (T)(1u | Word<T>::kFlag);
+        p.X0[v] = one;
+        p.X1[v] = one;
         p.colors_out[v] = 1;
         maxc = 1;
     }
@@ -382,6 +440,8 @@ __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
     NextLists nl;
     nl.S = p.SA; nl.M = p.MA; nl.H = p.HA; nl.Hc = p.HcA; nl.O = p.OA;
     nl.cnt = p.st->cnt[2];
+    nl.s_max = p.s_max;
+    nl.m_max = p.m_max;
     return nl;
 }
 
@@ -389,8 +449,8 @@ __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
 // (rows of degree <= kPass1Flat) are read as one flat, coalesced range;
 // lane l of batch u handles flat entry F0 + 32u + l, finds its row by a
 // binary search over the rows' running totals, and the per-row conflict
-// flag is gathered from the batch ballot.  Larger rows go to the early-exit
-// list.
+// flag is gathered from the batch ballot.  Longer rows go to
+// pass1_long_kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
     const unsigned lane = lane_id();
@@ -407,8 +467,8 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
         const int32_t v = valid ? (int32_t)vv : 0;
         const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
         const int32_t d = valid ? __ldg(p.rowptr + v + 1) - b : 0;
-        const bool defer = d > kPass1Flat;
-        const int32_t eff = defer ? 0 : d;
+        const bool longrow = d > kPass1Flat;
+        const int32_t eff = longrow ? 0 : d;
         const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
         int32_t incl = eff;
 #pragma unroll
@@ -451,13 +511,13 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
                 }
             }
         }
-        if (valid && !defer) {
+        if (valid && !longrow) {
             pass1_write(p, v, hit, maxc);
             if (hit) vol += (unsigned)d;
         }
         const int bin = bin_of(d, p.s_max, p.m_max);
-        const bool go = valid && !defer && hit;
-        const int4 e = make_int4(v, b, d, -1);
+        const bool go = valid && !longrow && hit;
+        const int4 e = make_int4(v, b, d, d);
         warp_append(go && bin == kBinS, e, nl.S, &nl.cnt[kBinS]);
         warp_append(go && bin == kBinM, e, nl.M, &nl.cnt[kBinM]);
         // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
@@ -465,10 +525,10 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
         while (hubs) {
             const int j = __ffs(hubs) - 1;
             hubs &= hubs - 1;
-            warp_append_hub(nl, make_int4(__shfl_sync(kFull, v, j), __shfl_sync(kFull, b, j),
-                                          __shfl_sync(kFull, d, j), -1));
+            const int32_t dj = __shfl_sync(kFull, d, j);
+            warp_append_hub(nl, make_int4(__shfl_sync(kFull, v, j), __shfl_sync(kFull, b, j), dj, dj));
         }
-        warp_append_i32(valid && defer, v, p.defer, &p.st->defer_cnt);
+        warp_append_i32(valid && longrow, v, p.defer, &p.st->defer_cnt);
     }
     fold_max_color(p.st, maxc);
     fold_volume(p.round_vol, p.round_cap, 2, vol);
@@ -477,7 +537,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
 // Round 1 for rows longer than kPass1Flat: one warp per vertex, 128
 // entries per step, stop at the first preceding neighbour.
 template <typename T>
-__global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
+__global__ void __launch_bounds__(256) pass1_long_kernel(Params<T> p) {
     const unsigned lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -505,15 +565,8 @@ __global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
         }
         if (lane == 0) pass1_write(p, v, conflict, maxc);
         if (conflict) {
-            const int bin = bin_of(e - b, p.s_max, p.m_max);
-            const int4 en = make_int4(v, b, e - b, -1);
             if (lane == 0) vol += (unsigned)(e - b);
-            if (bin == kBinH) {
-                warp_append_hub(nl, en);
-            } else if (lane == 0) {
-                int4* list = bin == kBinM ? nl.M : nl.S;
-                list[atomicAdd(&nl.cnt[bin], 1u)] = en;
-            }
+            warp_append_one(nl, make_int4(v, b, e - b, e - b));
         }
     }
     fold_max_color(p.st, maxc);
@@ -524,11 +577,15 @@ __global__ void __launch_bounds__(256) pass1_defer_kernel(Params<T> p) {
 
 template <typename T>
 struct PassIO {
-    const T* Xc;        // C_k
-    T* Xn;              // receives C_{k+1} (conflicting) or the final color (settled)
+    const T* Xc;            // C_k (flagged once settled)
+    T* Xcw;                 // the same array, for setting the settled flag
+    T* Xn;                  // receives C_{k+1}
+    const int32_t* rin;     // active lists read this round (colidx in round 2)
+    int32_t* rout;          // active lists written for the next round
+    bool first;             // round 2: no static masks yet
     const int4* S; const int4* M; const int4* H; const int32_t* Hc; const int32_t* O;
     NextLists next;
-    uint64_t pol_adj, pol_col;
+    uint64_t pol_row, pol_col;
 };
 
 template <typename T>
@@ -536,7 +593,11 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     PassIO<T> io;
     const bool odd = (k & 1) != 0;
     io.Xc = odd ? p.X1 : p.X0;
+    io.Xcw = odd ? p.X1 : p.X0;
     io.Xn = odd ? p.X0 : p.X1;
+    io.first = k == 2;
+    io.rin = k == 2 ? p.colidx : (odd ? p.act1 : p.act0);
+    io.rout = odd ? p.act0 : p.act1;
     io.S = odd ? p.SB : p.SA;
     io.M = odd ? p.MB : p.MA;
     io.H = odd ? p.HB : p.HA;
@@ -548,34 +609,46 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     io.next.Hc = odd ? p.HcA : p.HcB;
     io.next.O = odd ? p.OA : p.OB;
     io.next.cnt = p.st->cnt[(k + 1) % 3];
-    io.pol_adj = policy_evict_first();
+    io.next.s_max = p.s_max;
+    io.next.m_max = p.m_max;
+    io.pol_row = policy_evict_first();
     io.pol_col = policy_evict_last();
     return io;
 }
 
+// v settles with color cv: flag it in both buffers, publish it.
 template <typename T>
-__device__ __forceinline__ void settle(const Params<T>& p, const PassIO<T>& io, int32_t v, T cv) {
-    io.Xn[v] = cv;
+__device__ __forceinline__ void settle(const Params<T>& p, const PassIO<T>& io, int32_t v, uint32_t cv) {
+    const T word = (T)(cv | Word<T>::kFlag);
+    io.Xn[v] = word;
+    io.Xcw[v] = word;
     p.colors_out[v] = (int32_t)cv;
 }
 
-// What a warp needs to start a task: its worklist entry and, for an H-bin
-// chunk, the chunk's first entry.  Loaded one task ahead.
+// v takes color c in round k+1.
+template <typename T>
+__device__ __forceinline__ void recolor(const Params<T>& p, const PassIO<T>& io, int32_t v, uint32_t c) {
+    if (c >= p.color_limit) atomicExch(&p.st->status, kStatusColorOverflow);
+    io.Xn[v] = (T)(c & (Word<T>::kFlag - 1u));
+}
+
+// What a warp needs to start a task.  Loaded one task ahead.
 struct TaskHead {
-    int4 e;      // {vertex, row start, degree, 0}; x < 0 marks an empty S slot
-    int32_t lo;  // H chunk: first adjacency entry of the chunk
+    int4 e;       // {vertex, row start, active length, degree}; x < 0 marks an empty slot
+    int32_t pos;  // H chunk: worklist position of its vertex
+    int32_t lo;   // H chunk: first entry of the chunk
 };
 
 template <typename T>
 __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, unsigned nS,
                                               unsigned nM, unsigned nHC, unsigned tM) {
     TaskHead h;
+    h.pos = 0;
     h.lo = 0;
     if (t < nHC) {
-        const int32_t pos = __ldcg(io.O + t);
-        h.e = __ldcg(io.H + pos);
-        h.lo = h.e.y + ((int32_t)t - __ldcg(io.Hc + pos)) * kChunk;
-        h.e.w = pos;
+        h.pos = __ldcg(io.O + t);
+        h.e = __ldcg(io.H + h.pos);
+        h.lo = h.e.y + ((int32_t)t - __ldcg(io.Hc + h.pos)) * kChunk;
     } else if (t - nHC < tM) {
         const unsigned i = (t - nHC) * 32 + lane_id();
         h.e = i < nM ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
@@ -586,38 +659,54 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
     return h;
 }
 
-// S and M bins: 32 worklist entries per task, one per lane.  Their rows are
-// walked as one flat range in batches of 32 entries (lane l of batch u takes
-// flat entry F0 + 32u + l and finds its row by binary search over the rows'
-// running totals), so every lane has an entry in every batch whatever the
-// degrees are.  Each entry ORs its neighbour's color into its row's 256-bit
-// window in shared memory and flags a conflict; afterwards each lane decides
-// its own vertex.  First fit <= degree + 1 <= 257, so only a row of degree
-// 256 can find the window full, and then it rescans.
-constexpr int kFlatBatches = 4;       // batches whose loads are in flight together
-constexpr int kWarpsPerBlockMax = 8;  // block_threads <= 256
+// Shared memory of one warp for a flat task.
+struct FlatSmem {
+    uint32_t stat[32 * 8];  // per entry vertex: static mask (+ colors settled this round)
+    uint32_t dyn[32 * 8];   // per entry vertex: colors of unsettled neighbours this round
+};
 
+// S and M bins: 32 worklist entries per task, one per lane.  Their active
+// lists are walked as one flat range in batches of 32 entries (lane l of
+// batch u takes flat entry F0 + 32u + l and finds its list by binary search
+// over the lists' running totals), so every lane has an entry in every batch
+// whatever the lengths are.  Each entry ORs its neighbour's color into its
+// vertex's window in shared memory, flags a conflict, and, if the neighbour
+// has not settled, is copied to the next round's list at the vertex's
+// running write position.  Afterwards each lane decides its own vertex.
 template <typename T>
 __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en, int bin,
-                                          uint32_t* smask, uint32_t* sconf, int& maxc,
-                                          unsigned& vol) {
+                                          FlatSmem& sm, int& maxc, unsigned& vol) {
     const unsigned lane = lane_id();
     const bool valid = en.x >= 0;
     const int32_t v = valid ? en.x : 0;
     const int32_t b = en.y;
-    const int32_t d = valid ? en.z : 0;
-    const T cv = valid ? ld_color(io.Xc + v, io.pol_col) : (T)0;
+    const int32_t len = valid ? en.z : 0;
+    const uint32_t cv = valid ? word_color(ld_color(io.Xc + v, io.pol_col)) : 0u;
+    // static mask of v (none yet in round 2)
+    if (valid && !io.first) {
+        const uint4* src = reinterpret_cast<const uint4*>(p.stat + (size_t)v * 8);
+        const uint4 a = __ldcg(src), c = __ldcg(src + 1);
+        sm.stat[lane * 8 + 0] = a.x; sm.stat[lane * 8 + 1] = a.y;
+        sm.stat[lane * 8 + 2] = a.z; sm.stat[lane * 8 + 3] = a.w;
+        sm.stat[lane * 8 + 4] = c.x; sm.stat[lane * 8 + 5] = c.y;
+        sm.stat[lane * 8 + 6] = c.z; sm.stat[lane * 8 + 7] = c.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) smask[lane * 8 + q] = 0u;
-    if (lane == 0) *sconf = 0u;
-    int32_t incl = d;
+        for (int q = 0; q < 8; ++q) sm.stat[lane * 8 + q] = 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sm.dyn[lane * 8 + q] = 0u;
+    int32_t incl = len;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int32_t x = __shfl_up_sync(kFull, incl, o);
         if ((int)lane >= o) incl += x;
     }
-    const int32_t off = incl - d;
+    const int32_t off = incl - len;
     const int32_t D = __shfl_sync(kFull, incl, 31);
+    int32_t kept = 0;      // entries of this lane's vertex written for the next round
+    bool conflict = false; // this lane's vertex has a preceding neighbour of its color
+    bool dirty = false;    // this lane's vertex met a newly settled neighbour
     __syncwarp();
     for (int32_t F0 = 0; F0 < D; F0 += 32 * kFlatBatches) {
         int32_t w[kFlatBatches], own[kFlatBatches];
@@ -634,117 +723,191 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             own[u] = lo;
             const int32_t ob = __shfl_sync(kFull, b, lo);
             const int32_t oo = __shfl_sync(kFull, off, lo);
-            w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), io.pol_adj) : -1;
+            w[u] = f < D ? ld_row(io.rin + ob + (f - oo), io.pol_row) : 0;
         }
         T c[kFlatBatches];
 #pragma unroll
-        for (int u = 0; u < kFlatBatches; ++u)
-            c[u] = w[u] >= 0 ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+        for (int u = 0; u < kFlatBatches; ++u) {
+            const int32_t f = F0 + 32 * u + (int32_t)lane;
+            c[u] = f < D ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+        }
 #pragma unroll
         for (int u = 0; u < kFlatBatches; ++u) {
-            const T ocv = __shfl_sync(kFull, cv, own[u]);
-            const int32_t ov = __shfl_sync(kFull, v, own[u]);
-            if (w[u] >= 0) {
-                if (c[u] == ocv &&
-                    precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u))
-                    atomicOr(sconf, 1u << own[u]);
-                const unsigned idx = (unsigned)c[u] - 1u;
-                if (idx < 256u) atomicOr(&smask[own[u] * 8 + (idx >> 5)], 1u << (idx & 31u));
+            const int32_t base = F0 + 32 * u;
+            const int32_t f = base + (int32_t)lane;
+            const int o = own[u];
+            const uint32_t ocv = __shfl_sync(kFull, cv, o);
+            const int32_t ov = __shfl_sync(kFull, v, o);
+            const int32_t ob = __shfl_sync(kFull, b, o);
+            const int32_t oo = __shfl_sync(kFull, off, o);
+            const int32_t okept = __shfl_sync(kFull, kept, o);
+            const bool in = f < D;
+            const uint32_t col = word_color(c[u]);
+            const bool settled = in && word_settled(c[u]);
+            const bool hit = in && col == ocv &&
+                             precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u);
+            if (in) {
+                const unsigned idx = col - 1u;
+                if (idx < 256u) {
+                    const uint32_t bit = 1u << (idx & 31u);
+                    atomicOr(settled ? &sm.stat[o * 8 + (idx >> 5)] : &sm.dyn[o * 8 + (idx >> 5)], bit);
+                }
+            }
+            // survivors: copy to the next round's list, in order within each vertex
+            const bool keep = in && !settled;
+            const unsigned kb = __ballot_sync(kFull, keep);
+            const unsigned hb = __ballot_sync(kFull, hit);
+            const unsigned sb = __ballot_sync(kFull, settled);
+            const int32_t seglo = max(0, oo - base);  // first lane of my vertex in this batch
+            const unsigned below = kb & ((1u << lane) - 1u) & ~((1u << seglo) - 1u);
+            if (keep) io.rout[ob + okept + __popc(below)] = w[u];
+            // my vertex's lanes in this batch: [lo, hi)
+            const int32_t lo = max(0, min(32, off - base));
+            const int32_t hi = max(0, min(32, off + len - base));
+            if (hi > lo) {
+                const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
+                kept += __popc((kb >> lo) & bits);
+                conflict |= ((hb >> lo) & bits) != 0u;
+                dirty |= ((sb >> lo) & bits) != 0u;
             }
         }
     }
     __syncwarp();
-    const bool conflict = valid && ((*sconf >> lane) & 1u);
-    unsigned color = 0;
+    conflict = conflict && valid;
+    uint32_t color = 0;
     bool rescan = false;
     if (conflict) {
         int ff = -1;
 #pragma unroll
         for (int q = 7; q >= 0; --q) {
-            const uint32_t word = smask[lane * 8 + q];
+            const uint32_t word = sm.stat[lane * 8 + q] | sm.dyn[lane * 8 + q];
             if (word != 0xffffffffu) ff = q * 32 + __ffs(~word) - 1;
         }
-        if (ff >= 0) color = (unsigned)ff + 1u;
+        if (ff >= 0) color = (uint32_t)ff + 1u;
         else rescan = true;
     }
     unsigned need = __ballot_sync(kFull, rescan);
     while (need) {
         const int j = __ffs(need) - 1;
         need &= need - 1;
-        const int32_t jb = __shfl_sync(kFull, b, j), jd = __shfl_sync(kFull, d, j);
-        const unsigned cj = rescan_first_fit(p.colidx, io.Xc, jb, jb + jd);
+        const uint32_t cj = rescan_first_fit(p.rowptr, p.colidx, io.Xc, __shfl_sync(kFull, v, j));
         if ((int)lane == j) color = cj;
     }
     if (valid) {
         if (conflict) {
-            io.Xn[v] = (T)color;
-            vol += (unsigned)d;
+            recolor(p, io, v, color);
+            vol += (unsigned)kept;
+            if (io.first || dirty) {
+                uint4* dst = reinterpret_cast<uint4*>(p.stat + (size_t)v * 8);
+                dst[0] = make_uint4(sm.stat[lane * 8 + 0], sm.stat[lane * 8 + 1],
+                                    sm.stat[lane * 8 + 2], sm.stat[lane * 8 + 3]);
+                dst[1] = make_uint4(sm.stat[lane * 8 + 4], sm.stat[lane * 8 + 5],
+                                    sm.stat[lane * 8 + 6], sm.stat[lane * 8 + 7]);
+            }
         } else {
             settle(p, io, v, cv);
             maxc = max(maxc, (int)cv);
         }
     }
-    warp_append(conflict, en, bin == kBinS ? io.next.S : io.next.M, &io.next.cnt[bin]);
+    // next round: same row start, `kept` active entries; the bin may shrink
+    const int4 ne = make_int4(v, b, kept, en.w);
+    const int nb = bin_of(kept, p.s_max, p.m_max);
+    warp_append(conflict && nb == kBinS, ne, io.next.S, &io.next.cnt[kBinS]);
+    warp_append(conflict && nb == kBinM, ne, io.next.M, &io.next.cnt[kBinM]);
+    (void)bin;
     __syncwarp();
 }
 
-// H bin: one 256-entry chunk of the vertex at worklist position en.w.  The
+// H bin: one 256-entry chunk of the vertex at worklist position h.pos.  The
 // warp that completes the vertex's last chunk decides it and clears its record.
 template <typename T>
 __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
                                           int& maxc, unsigned& vol) {
     const unsigned lane = lane_id();
-    const int32_t v = h.e.x, b = h.e.y, e = h.e.y + h.e.z, pos = h.e.w;
+    const int32_t v = h.e.x, b = h.e.y, len = h.e.z;
+    const int32_t e = b + len;
     const int32_t lo = h.lo, hi = min(e, lo + kChunk);
     int32_t w[kPerLane];
 #pragma unroll
     for (int u = 0; u < kPerLane; ++u) {
         const int32_t j = lo + (int32_t)lane + 32 * u;
-        w[u] = j < hi ? ld_adj(p.colidx + j, io.pol_adj) : -1;
+        w[u] = j < hi ? ld_row(io.rin + j, io.pol_row) : 0;
     }
-    const T cv = ld_color(io.Xc + v, io.pol_col);
+    const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
     T c[kPerLane];
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u) c[u] = w[u] >= 0 ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+    for (int u = 0; u < kPerLane; ++u) {
+        const int32_t j = lo + (int32_t)lane + 32 * u;
+        c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+    }
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
     bool conflict = false;
-    Mask256 m;
+    Mask256 m, ms;
     m.clear();
+    ms.clear();
+    unsigned keepbits[kPerLane];
+    unsigned nkeep = 0;
 #pragma unroll
     for (int u = 0; u < kPerLane; ++u) {
-        if (w[u] >= 0) {
-            if (c[u] == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
-            m.set((unsigned)c[u] - 1u);
+        const int32_t j = lo + (int32_t)lane + 32 * u;
+        const bool in = j < hi;
+        const uint32_t col = word_color(c[u]);
+        const bool settled = in && word_settled(c[u]);
+        if (in) {
+            if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+            m.set(col - 1u);
+            if (settled) ms.set(col - 1u);
         }
+        keepbits[u] = __ballot_sync(kFull, in && !settled);
+        nkeep += __popc(keepbits[u]);
     }
     const bool any_conflict = __any_sync(kFull, conflict);
     const uint32_t word = m.warp_reduce_word();
-    HubRecord* rec = p.hubs + pos;
+    const uint32_t sword = ms.warp_reduce_word();
+    HubRecord* rec = p.hubs + h.pos;
+    // survivors go to [b + slot, b + slot + nkeep) of the next round's list
+    unsigned slot = 0;
+    if (lane == 0 && nkeep) slot = atomicAdd(&rec->kept, nkeep);
+    slot = __shfl_sync(kFull, slot, 0);
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+        if ((keepbits[u] >> lane) & 1u)
+            io.rout[b + slot + __popc(keepbits[u] & ((1u << lane) - 1u))] = w[u];
+        slot += __popc(keepbits[u]);
+    }
     if (lane < 8u && word) atomicOr(&rec->mask[lane], word);
+    if (lane < 8u && sword) atomicOr(&rec->stat[lane], sword);
     if (lane == 0 && any_conflict) atomicOr(&rec->conflict, 1u);
     __threadfence();
-    const unsigned nch = (unsigned)(e - b + kChunk - 1) / kChunk;
+    const unsigned nch = (unsigned)(len + kChunk - 1) / kChunk;
     unsigned done = 0;
     if (lane == 0) done = atomicAdd(&rec->done, 1u);
     done = __shfl_sync(kFull, done, 0);
     if (done != nch - 1) return;
     // last chunk of v: decide
     __threadfence();
-    const uint32_t all = lane < 8u ? __ldcg(&rec->mask[lane & 7u]) : 0u;
     const bool conf = __ldcg(&rec->conflict) != 0u;
-    if (lane < 16u) ((unsigned*)rec)[lane] = 0u;  // reset for the next round
+    const int32_t kept = (int32_t)__ldcg(&rec->kept);
+    uint32_t all = 0, stat = 0;
+    if (lane < 8u) {
+        const uint32_t old = io.first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
+        stat = old | __ldcg(&rec->stat[lane]);
+        all = stat | __ldcg(&rec->mask[lane]);
+    }
+    if (lane < 32u) ((unsigned*)rec)[lane] = 0u;  // reset for the next round
     if (!conf) {
         if (lane == 0) settle(p, io, v, cv);
         maxc = max(maxc, (int)cv);
         return;
     }
     const int ff = window_first_clear(all);
-    const unsigned color = ff >= 0 ? (unsigned)ff + 1u : rescan_first_fit(p.colidx, io.Xc, b, e);
+    const uint32_t color = ff >= 0 ? (uint32_t)ff + 1u : rescan_first_fit(p.rowptr, p.colidx, io.Xc, v);
+    if (lane < 8u) p.stat[(size_t)v * 8 + lane] = stat;
     if (lane == 0) {
-        io.Xn[v] = (T)color;
-        vol += (unsigned)(e - b);
+        recolor(p, io, v, color);
+        vol += (unsigned)kept;
     }
-    warp_append_hub(io.next, make_int4(v, b, e - b, -1));
+    warp_append_one(io.next, make_int4(v, b, kept, h.e.w));
 }
 
 // One fused pass over U_k.  Task t: first the H-bin chunks, then the M-bin
@@ -753,15 +916,14 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 template <typename T>
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc) {
-    __shared__ uint32_t s_mask[kWarpsPerBlockMax][32 * 8];
-    __shared__ uint32_t s_conf[kWarpsPerBlockMax];
+    __shared__ FlatSmem s_flat[kWarpsPerBlockMax];
     const PassIO<T> io = pass_io(p, k);
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned W = (gridDim.x * blockDim.x) >> 5;
     const unsigned wib = threadIdx.x >> 5;
     const unsigned tM = (nM + 31) / 32, tS = (nS + 31) / 32;
     const unsigned total = nHC + tM + tS;
-    unsigned vol = 0;  // this lane's share of vol(U_{k+1})
+    unsigned vol = 0;  // this lane's share of the next round's read volume
     TaskHead cur;
     if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM);
     for (unsigned t = gw; t < total; t += W) {
@@ -771,7 +933,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         if (t < nHC) {
             hub_chunk(p, io, cur, maxc, vol);
         } else {
-            flat_task(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_mask[wib], &s_conf[wib], maxc, vol);
+            flat_task(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_flat[wib], maxc, vol);
         }
         cur = nxt;
     }
@@ -779,10 +941,10 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
 }
 
 // All rounds k >= 2 in one cooperative launch; a bounded grid barrier
-// separates the rounds.  Every block reads the same counts after a barrier,
-// so all blocks leave the loop in the same round.
+// separates the rounds.  Every block reads the same counts and status after
+// a barrier, so all blocks leave the loop in the same round.
 template <typename T>
-__global__ void __launch_bounds__(256, 5) rounds_persistent_kernel(Params<T> p) {
+__global__ void __launch_bounds__(256, 4) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
     for (int k = 2;; ++k) {
@@ -794,6 +956,7 @@ __global__ void __launch_bounds__(256, 5) rounds_persistent_kernel(Params<T> p) 
             if (blockIdx.x == 0 && threadIdx.x == 0) st->rounds = k - 1;
             break;
         }
+        if (__ldcg(&st->status) == kStatusColorOverflow) break;
         if (k > p.max_rounds) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->rounds = k - 1;
@@ -814,8 +977,8 @@ __global__ void __launch_bounds__(256, 5) rounds_persistent_kernel(Params<T> p) 
 
 // One pass per launch (loop mode 1): counts come from the host.
 template <typename T>
-__global__ void __launch_bounds__(256, 5) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
-                                                    unsigned nHC) {
+__global__ void __launch_bounds__(256, 4) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
+                                                       unsigned nHC) {
     int maxc = 0;
     run_pass(p, k, nS, nM, nHC, maxc);
     fold_max_color(p.st, maxc);

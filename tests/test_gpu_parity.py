@@ -83,6 +83,8 @@ def test_parity_with_priority(gcpkg, make):
     {"small_max_degree": 1, "medium_max_degree": 256},   # nearly everything warp-per-vertex
     {"small_max_degree": 5, "medium_max_degree": 40},
     {"block_threads": 128},
+    {"narrow_color_limit": 3},                           # restart with 32-bit state
+    {"narrow_color_limit": 200, "loop_mode": 1},
 ])
 def test_parity_launch_variants(gcpkg, opts):
     for g in [gg.rmat(13, 8, gg.RMAT_B, 7), gg.complete(300), gg.gnm(3000, 30000, 9)]:
