@@ -201,7 +201,7 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
                                     cudaMemcpyHostToDevice, s));
         }
         GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 4 * sizeof(unsigned), s));
-        const int64_t tasks = (int64_t)nHC + (nM + 31) / 32 + (nS + 31) / 32;
+        const int64_t tasks = (int64_t)nHC + (nM + gc::kMedPerTask - 1) / gc::kMedPerTask + (nS + 31) / 32;
         const int64_t warps_per_block = threads / 32;
         const int grid = (int)std::max<int64_t>(
             1, std::min<int64_t>((tasks + warps_per_block - 1) / warps_per_block, (int64_t)dc.sms * 8));

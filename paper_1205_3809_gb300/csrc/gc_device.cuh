@@ -30,7 +30,8 @@
 //
 // Work is split into warp-sized tasks, binned by the current active length:
 //   S bin (length <= s_max <= 32) and M bin (s_max < length <= m_max <= 256):
-//     32 worklist entries per task, their lists walked as one flat range;
+//     32 (S) or 4 (M) worklist entries per task, their lists walked as one
+//     flat range;
 //   H bin (length > m_max): one 256-entry chunk of one list per task; the
 //     chunks of a vertex OR their conflict flag and color windows into a
 //     per-vertex record, write their survivors at offsets taken from an
@@ -52,6 +53,7 @@ constexpr int kMedMaxLimit = 32 * kPerLane;   // M bin: length <= 256
 constexpr int kChunk = 32 * kPerLane;         // 256 entries per H-bin task
 constexpr int kPass1Flat = 256;               // pass 1: longer rows take the per-warp path
 constexpr int kFlatBatches = 4;               // flat tasks: batches in flight together
+constexpr int kMedPerTask = 4;                // M-bin vertices per task (<= 1024 entries)
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
 
 // Status codes shared with gc.h (kept numerically equal), and one internal.
@@ -650,8 +652,8 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
         h.e = __ldcg(io.H + h.pos);
         h.lo = h.e.y + ((int32_t)t - __ldcg(io.Hc + h.pos)) * kChunk;
     } else if (t - nHC < tM) {
-        const unsigned i = (t - nHC) * 32 + lane_id();
-        h.e = i < nM ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
+        const unsigned i = (t - nHC) * kMedPerTask + lane_id();
+        h.e = (lane_id() < (unsigned)kMedPerTask && i < nM) ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
     } else {
         const unsigned i = (t - nHC - tM) * 32 + lane_id();
         h.e = i < nS ? __ldcg(io.S + i) : make_int4(-1, 0, 0, 0);
@@ -663,16 +665,29 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
 struct FlatSmem {
     uint32_t stat[32 * 8];  // per entry vertex: static mask (+ colors settled this round)
     uint32_t dyn[32 * 8];   // per entry vertex: colors of unsettled neighbours this round
+    uint32_t conf;          // per entry vertex: conflict flag
+    uint32_t lane_of[32];   // lane of the i-th non-empty row
+    int32_t vid[32];        // vertex of each lane
 };
 
-// S and M bins: 32 worklist entries per task, one per lane.  Their active
-// lists are walked as one flat range in batches of 32 entries (lane l of
-// batch u takes flat entry F0 + 32u + l and finds its list by binary search
-// over the lists' running totals), so every lane has an entry in every batch
-// whatever the lengths are.  Each entry ORs its neighbour's color into its
-// vertex's window in shared memory, flags a conflict, and, if the neighbour
-// has not settled, is copied to the next round's list at the vertex's
-// running write position.  Afterwards each lane decides its own vertex.
+// Stores of the next round's active lists and static masks: read once, in
+// the next round, so evicted first.
+__device__ __forceinline__ void st_stream(int32_t* a, int32_t x, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" :: "l"(a), "r"(x), "l"(pol) : "memory");
+}
+
+// S and M bins: up to 32 worklist entries per task, one per lane.  Their
+// active lists are walked as one flat range in batches of 32 entries (lane
+// l of batch u takes flat entry F0 + 32u + l), so every lane has an entry in
+// every batch whatever the lengths are.  The row owning an entry is found
+// from the batch's row starts: a row that starts inside the batch sets the
+// bit of its first lane (one OR-reduction over the warp), and an entry's
+// row is the last one started at or before it, counted among the non-empty
+// rows (a 32-entry table maps that count to the row's lane).  Each entry ORs its neighbour's color into
+// its vertex's window in shared memory, flags a conflict, and, if the
+// neighbour has not settled, is copied to the next round's list at the
+// vertex's running write position.  Afterwards each lane decides its own
+// vertex.
 template <typename T>
 __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en, int bin,
                                           FlatSmem& sm, int& maxc, unsigned& vol) {
@@ -696,6 +711,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) sm.dyn[lane * 8 + q] = 0u;
+    if (lane == 0) sm.conf = 0u;
     int32_t incl = len;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -704,26 +720,27 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     }
     const int32_t off = incl - len;
     const int32_t D = __shfl_sync(kFull, incl, 31);
-    int32_t kept = 0;      // entries of this lane's vertex written for the next round
-    bool conflict = false; // this lane's vertex has a preceding neighbour of its color
-    bool dirty = false;    // this lane's vertex met a newly settled neighbour
+    const unsigned nz = __ballot_sync(kFull, len > 0);  // rows that own entries
+    if (len > 0) sm.lane_of[__popc(nz & ((1u << lane) - 1u))] = lane;
+    sm.vid[lane] = v;
+    int32_t kept = 0;  // entries of this lane's vertex written for the next round
     __syncwarp();
     for (int32_t F0 = 0; F0 < D; F0 += 32 * kFlatBatches) {
-        int32_t w[kFlatBatches], own[kFlatBatches];
+        int32_t w[kFlatBatches], own[kFlatBatches], ob[kFlatBatches], oo[kFlatBatches];
 #pragma unroll
         for (int u = 0; u < kFlatBatches; ++u) {
-            const int32_t f = F0 + 32 * u + (int32_t)lane;
-            int lo = 0, hi = 31;
-#pragma unroll
-            for (int s = 0; s < 5; ++s) {
-                const int mid = (lo + hi) >> 1;
-                const int32_t val = __shfl_sync(kFull, incl, mid);
-                if (val > f) hi = mid; else lo = mid + 1;
-            }
-            own[u] = lo;
-            const int32_t ob = __shfl_sync(kFull, b, lo);
-            const int32_t oo = __shfl_sync(kFull, off, lo);
-            w[u] = f < D ? ld_row(io.rin + ob + (f - oo), io.pol_row) : 0;
+            const int32_t base = F0 + 32 * u;
+            const int32_t f = base + (int32_t)lane;
+            // rows started before this batch, and the starts inside it
+            const int32_t rel = off - base;
+            const unsigned before = __popc(__ballot_sync(kFull, len > 0 && rel < 0));
+            const unsigned starts = __reduce_or_sync(kFull, (len > 0 && rel >= 0 && rel < 32) ? (1u << rel) : 0u);
+            const unsigned rank = before + __popc(starts & (0xffffffffu >> (31 - lane)));
+            const int o = (f < D && rank > 0) ? (int)sm.lane_of[rank - 1] : 0;
+            own[u] = o;
+            ob[u] = __shfl_sync(kFull, b, o);
+            oo[u] = __shfl_sync(kFull, off, o);
+            w[u] = f < D ? ld_row(io.rin + ob[u] + (f - oo[u]), io.pol_row) : 0;
         }
         T c[kFlatBatches];
 #pragma unroll
@@ -737,43 +754,38 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             const int32_t f = base + (int32_t)lane;
             const int o = own[u];
             const uint32_t ocv = __shfl_sync(kFull, cv, o);
-            const int32_t ov = __shfl_sync(kFull, v, o);
-            const int32_t ob = __shfl_sync(kFull, b, o);
-            const int32_t oo = __shfl_sync(kFull, off, o);
             const int32_t okept = __shfl_sync(kFull, kept, o);
             const bool in = f < D;
             const uint32_t col = word_color(c[u]);
             const bool settled = in && word_settled(c[u]);
-            const bool hit = in && col == ocv &&
-                             precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u);
             if (in) {
-                const unsigned idx = col - 1u;
-                if (idx < 256u) {
-                    const uint32_t bit = 1u << (idx & 31u);
-                    atomicOr(settled ? &sm.stat[o * 8 + (idx >> 5)] : &sm.dyn[o * 8 + (idx >> 5)], bit);
+                if (col == ocv) {
+                    const int32_t ov = sm.vid[o];
+                    if (precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u))
+                        atomicOr(&sm.conf, 1u << o);
                 }
+                const unsigned idx = col - 1u;
+                if (idx < 256u)
+                    atomicOr(settled ? &sm.stat[o * 8 + (idx >> 5)] : &sm.dyn[o * 8 + (idx >> 5)],
+                             1u << (idx & 31u));
             }
             // survivors: copy to the next round's list, in order within each vertex
             const bool keep = in && !settled;
             const unsigned kb = __ballot_sync(kFull, keep);
-            const unsigned hb = __ballot_sync(kFull, hit);
-            const unsigned sb = __ballot_sync(kFull, settled);
-            const int32_t seglo = max(0, oo - base);  // first lane of my vertex in this batch
+            const int32_t seglo = max(0, oo[u] - base);  // first lane of my vertex in this batch
             const unsigned below = kb & ((1u << lane) - 1u) & ~((1u << seglo) - 1u);
-            if (keep) io.rout[ob + okept + __popc(below)] = w[u];
+            if (keep) st_stream(io.rout + ob[u] + okept + __popc(below), w[u], io.pol_row);
             // my vertex's lanes in this batch: [lo, hi)
             const int32_t lo = max(0, min(32, off - base));
             const int32_t hi = max(0, min(32, off + len - base));
             if (hi > lo) {
                 const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
                 kept += __popc((kb >> lo) & bits);
-                conflict |= ((hb >> lo) & bits) != 0u;
-                dirty |= ((sb >> lo) & bits) != 0u;
             }
         }
     }
     __syncwarp();
-    conflict = conflict && valid;
+    const bool conflict = valid && ((sm.conf >> lane) & 1u);
     uint32_t color = 0;
     bool rescan = false;
     if (conflict) {
@@ -797,13 +809,11 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
         if (conflict) {
             recolor(p, io, v, color);
             vol += (unsigned)kept;
-            if (io.first || dirty) {
-                uint4* dst = reinterpret_cast<uint4*>(p.stat + (size_t)v * 8);
-                dst[0] = make_uint4(sm.stat[lane * 8 + 0], sm.stat[lane * 8 + 1],
-                                    sm.stat[lane * 8 + 2], sm.stat[lane * 8 + 3]);
-                dst[1] = make_uint4(sm.stat[lane * 8 + 4], sm.stat[lane * 8 + 5],
-                                    sm.stat[lane * 8 + 6], sm.stat[lane * 8 + 7]);
-            }
+            uint4* dst = reinterpret_cast<uint4*>(p.stat + (size_t)v * 8);
+            dst[0] = make_uint4(sm.stat[lane * 8 + 0], sm.stat[lane * 8 + 1],
+                                sm.stat[lane * 8 + 2], sm.stat[lane * 8 + 3]);
+            dst[1] = make_uint4(sm.stat[lane * 8 + 4], sm.stat[lane * 8 + 5],
+                                sm.stat[lane * 8 + 6], sm.stat[lane * 8 + 7]);
         } else {
             settle(p, io, v, cv);
             maxc = max(maxc, (int)cv);
@@ -818,63 +828,68 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     __syncwarp();
 }
 
-// H bin: one 256-entry chunk of the vertex at worklist position h.pos.  The
-// warp that completes the vertex's last chunk decides it and clears its record.
+// H bin: one 256-entry chunk of the vertex at worklist position h.pos, read
+// in two halves of 4 entries per lane.  The warp that completes the vertex's
+// last chunk decides it and clears its record.
 template <typename T>
 __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
                                           int& maxc, unsigned& vol) {
+    constexpr int kHalf = kPerLane / 2;
     const unsigned lane = lane_id();
     const int32_t v = h.e.x, b = h.e.y, len = h.e.z;
     const int32_t e = b + len;
     const int32_t lo = h.lo, hi = min(e, lo + kChunk);
-    int32_t w[kPerLane];
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        const int32_t j = lo + (int32_t)lane + 32 * u;
-        w[u] = j < hi ? ld_row(io.rin + j, io.pol_row) : 0;
-    }
     const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
-    T c[kPerLane];
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        const int32_t j = lo + (int32_t)lane + 32 * u;
-        c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
-    }
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
     bool conflict = false;
     Mask256 m, ms;
     m.clear();
     ms.clear();
-    unsigned keepbits[kPerLane];
-    unsigned nkeep = 0;
+    HubRecord* rec = p.hubs + h.pos;
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        const int32_t j = lo + (int32_t)lane + 32 * u;
-        const bool in = j < hi;
-        const uint32_t col = word_color(c[u]);
-        const bool settled = in && word_settled(c[u]);
-        if (in) {
-            if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
-            m.set(col - 1u);
-            if (settled) ms.set(col - 1u);
+    for (int half = 0; half < 2; ++half) {
+        int32_t w[kHalf];
+        T c[kHalf];
+        unsigned keepbits[kHalf];
+#pragma unroll
+        for (int u = 0; u < kHalf; ++u) {
+            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
+            w[u] = j < hi ? ld_row(io.rin + j, io.pol_row) : 0;
         }
-        keepbits[u] = __ballot_sync(kFull, in && !settled);
-        nkeep += __popc(keepbits[u]);
+#pragma unroll
+        for (int u = 0; u < kHalf; ++u) {
+            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
+            c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+        }
+        unsigned nkeep = 0;
+#pragma unroll
+        for (int u = 0; u < kHalf; ++u) {
+            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
+            const bool in = j < hi;
+            const uint32_t col = word_color(c[u]);
+            const bool settled = in && word_settled(c[u]);
+            if (in) {
+                if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+                m.set(col - 1u);
+                if (settled) ms.set(col - 1u);
+            }
+            keepbits[u] = __ballot_sync(kFull, in && !settled);
+            nkeep += __popc(keepbits[u]);
+        }
+        // survivors go to [b + slot, b + slot + nkeep) of the next round's list
+        unsigned slot = 0;
+        if (lane == 0 && nkeep) slot = atomicAdd(&rec->kept, nkeep);
+        slot = __shfl_sync(kFull, slot, 0);
+#pragma unroll
+        for (int u = 0; u < kHalf; ++u) {
+            if ((keepbits[u] >> lane) & 1u)
+                st_stream(io.rout + b + slot + __popc(keepbits[u] & ((1u << lane) - 1u)), w[u], io.pol_row);
+            slot += __popc(keepbits[u]);
+        }
     }
     const bool any_conflict = __any_sync(kFull, conflict);
     const uint32_t word = m.warp_reduce_word();
     const uint32_t sword = ms.warp_reduce_word();
-    HubRecord* rec = p.hubs + h.pos;
-    // survivors go to [b + slot, b + slot + nkeep) of the next round's list
-    unsigned slot = 0;
-    if (lane == 0 && nkeep) slot = atomicAdd(&rec->kept, nkeep);
-    slot = __shfl_sync(kFull, slot, 0);
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-        if ((keepbits[u] >> lane) & 1u)
-            io.rout[b + slot + __popc(keepbits[u] & ((1u << lane) - 1u))] = w[u];
-        slot += __popc(keepbits[u]);
-    }
     if (lane < 8u && word) atomicOr(&rec->mask[lane], word);
     if (lane < 8u && sword) atomicOr(&rec->stat[lane], sword);
     if (lane == 0 && any_conflict) atomicOr(&rec->conflict, 1u);
@@ -894,7 +909,7 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
         stat = old | __ldcg(&rec->stat[lane]);
         all = stat | __ldcg(&rec->mask[lane]);
     }
-    if (lane < 32u) ((unsigned*)rec)[lane] = 0u;  // reset for the next round
+    ((unsigned*)rec)[lane] = 0u;  // reset for the next round (32 words)
     if (!conf) {
         if (lane == 0) settle(p, io, v, cv);
         maxc = max(maxc, (int)cv);
@@ -911,8 +926,10 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 }
 
 // One fused pass over U_k.  Task t: first the H-bin chunks, then the M-bin
-// and S-bin entries 32 at a time; warp w takes t = w, w + W, ... and loads
-// the head of its next task before working on the current one.
+// entries kMedPerTask at a time, then the S-bin entries 32 at a time (every
+// task reads at most 1024 entries, so no warp holds up the end of a round);
+// warp w takes t = w, w + W, ... and loads the head of its next task before
+// working on the current one.
 template <typename T>
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc) {
@@ -921,7 +938,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned W = (gridDim.x * blockDim.x) >> 5;
     const unsigned wib = threadIdx.x >> 5;
-    const unsigned tM = (nM + 31) / 32, tS = (nS + 31) / 32;
+    const unsigned tM = (nM + kMedPerTask - 1) / kMedPerTask, tS = (nS + 31) / 32;
     const unsigned total = nHC + tM + tS;
     unsigned vol = 0;  // this lane's share of the next round's read volume
     TaskHead cur;
