@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
-LIB_PATH = os.path.join(_HERE, "libgc.so")
+LIB_PATH = os.environ.get("GC_LIB_PATH") or os.path.join(_HERE, "libgc.so")
 
 GC_OK = 0
 GC_ERR_INVALID = -1

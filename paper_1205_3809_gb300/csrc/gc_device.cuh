@@ -32,10 +32,11 @@
 //   S bin (length <= s_max <= 32) and M bin (s_max < length <= m_max <= 256):
 //     32 (S) or 4 (M) worklist entries per task, their lists walked as one
 //     flat range;
-//   H bin (length > m_max): one 256-entry chunk of one list per task; the
-//     chunks of a vertex OR their conflict flag and color windows into a
-//     per-vertex record, write their survivors at offsets taken from an
-//     atomic counter, and the warp that finishes the last chunk decides.
+//   H bin (length > m_max): one chunk of up to 1024 entries of one list per
+//     task; a list of one chunk is decided by its warp, and the chunks of a
+//     longer list OR their conflict flag and color windows into a per-vertex
+//     record, write their survivors at offsets taken from an atomic counter,
+//     and the warp that finishes the last chunk decides.
 // Tasks are dealt to warps round-robin; no block-wide barrier is taken
 // inside a round.
 #pragma once
@@ -50,10 +51,21 @@ constexpr int kBinS = 0, kBinM = 1, kBinH = 2;
 constexpr int kPerLane = 8;                   // adjacency entries per lane in a hub chunk
 constexpr int kSmallMaxLimit = 32;            // S bin: length <= 32
 constexpr int kMedMaxLimit = 32 * kPerLane;   // M bin: length <= 256
-constexpr int kChunk = 32 * kPerLane;         // 256 entries per H-bin task
+constexpr int kHubSub = 32 * kPerLane;        // 256 entries: one sub-block of a hub chunk
+constexpr int kChunk = 4 * kHubSub;           // 1024 entries per H-bin task
 constexpr int kPass1Flat = 256;               // pass 1: longer rows take the per-warp path
-constexpr int kFlatBatches = 4;               // flat tasks: batches in flight together
-constexpr int kMedPerTask = 4;                // M-bin vertices per task (<= 1024 entries)
+#ifndef GC_FLAT_BATCHES
+#define GC_FLAT_BATCHES 4
+#endif
+#ifndef GC_MIN_BLOCKS
+#define GC_MIN_BLOCKS 4
+#endif
+#ifndef GC_MED_PER_TASK
+#define GC_MED_PER_TASK 4
+#endif
+constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
+constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task (<= 1024 entries)
+constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
 
 // Status codes shared with gc.h (kept numerically equal), and one internal.
@@ -158,12 +170,22 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     return pol;
 }
 
+#ifndef GC_L1_COLORS
+#define GC_L1_COLORS 1
+#endif
+
 // Adjacency / active-list entry.  colidx is read-only for the whole call;
-// an active list is written in one round and read in the next, within the
-// same launch, so it is read at L2 (.cg).
+// an active list is written in one round and read in the next.  Rounds are
+// separated by kernel boundaries or by grid_barrier, whose fences make
+// earlier rounds' writes visible to cached loads after it (the ordering a
+// grid-wide synchronisation gives), so these loads may use L1.
 __device__ __forceinline__ int32_t ld_row(const int32_t* a, uint64_t pol) {
     int32_t r;
+#if GC_L1_COLORS
+    asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+#else
     asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+#endif
     return r;
 }
 __device__ __forceinline__ int32_t ld_adj(const int32_t* a, uint64_t pol) {
@@ -172,16 +194,27 @@ __device__ __forceinline__ int32_t ld_adj(const int32_t* a, uint64_t pol) {
     return r;
 }
 
-// Color word: written by other blocks in earlier rounds of the same launch,
-// so it is read at L2 (.cg), where it is kept (evict_last).
+// Color word: written in earlier rounds (visible after the round boundary,
+// as above) and kept in L2 (evict_last); the few high-degree vertices that
+// most gathers hit stay in each SM's L1.  Within a round a word may gain its
+// settled flag while others read it; a copy without the flag is still the
+// right color, and the flag is seen a round later.
 __device__ __forceinline__ uint16_t ld_color(const uint16_t* a, uint64_t pol) {
     uint16_t r;
+#if GC_L1_COLORS
+    asm volatile("ld.global.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(a), "l"(pol));
+#else
     asm volatile("ld.global.cg.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(a), "l"(pol));
+#endif
     return r;
 }
 __device__ __forceinline__ int32_t ld_color(const int32_t* a, uint64_t pol) {
     int32_t r;
+#if GC_L1_COLORS
+    asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+#else
     asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+#endif
     return r;
 }
 
@@ -828,9 +861,11 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     __syncwarp();
 }
 
-// H bin: one 256-entry chunk of the vertex at worklist position h.pos, read
-// in two halves of 4 entries per lane.  The warp that completes the vertex's
-// last chunk decides it and clears its record.
+// H bin: one chunk of up to 1024 entries of the vertex at worklist position
+// h.pos, read in sub-blocks of 256 (two halves of 4 entries per lane).  A
+// vertex whose active list fits one chunk is decided by this warp at once;
+// otherwise the chunks OR their results into the vertex's record, and the
+// warp that completes the last chunk decides it and clears the record.
 template <typename T>
 __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
                                           int& maxc, unsigned& vol) {
@@ -839,6 +874,8 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     const int32_t v = h.e.x, b = h.e.y, len = h.e.z;
     const int32_t e = b + len;
     const int32_t lo = h.lo, hi = min(e, lo + kChunk);
+    const unsigned nch = (unsigned)(len + kChunk - 1) / kChunk;
+    const bool single = nch == 1;
     const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
     bool conflict = false;
@@ -846,70 +883,87 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     m.clear();
     ms.clear();
     HubRecord* rec = p.hubs + h.pos;
+    unsigned local = 0;  // survivors written so far (single-chunk vertex)
+    for (int32_t sb = lo; sb < hi; sb += kHubSub) {
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        int32_t w[kHalf];
-        T c[kHalf];
-        unsigned keepbits[kHalf];
+        for (int half = 0; half < 2; ++half) {
+            int32_t w[kHalf];
+            T c[kHalf];
+            unsigned keepbits[kHalf];
 #pragma unroll
-        for (int u = 0; u < kHalf; ++u) {
-            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
-            w[u] = j < hi ? ld_row(io.rin + j, io.pol_row) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kHalf; ++u) {
-            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
-            c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
-        }
-        unsigned nkeep = 0;
-#pragma unroll
-        for (int u = 0; u < kHalf; ++u) {
-            const int32_t j = lo + (int32_t)lane + 32 * (half * kHalf + u);
-            const bool in = j < hi;
-            const uint32_t col = word_color(c[u]);
-            const bool settled = in && word_settled(c[u]);
-            if (in) {
-                if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
-                m.set(col - 1u);
-                if (settled) ms.set(col - 1u);
+            for (int u = 0; u < kHalf; ++u) {
+                const int32_t j = sb + (int32_t)lane + 32 * (half * kHalf + u);
+                w[u] = j < hi ? ld_row(io.rin + j, io.pol_row) : 0;
             }
-            keepbits[u] = __ballot_sync(kFull, in && !settled);
-            nkeep += __popc(keepbits[u]);
-        }
-        // survivors go to [b + slot, b + slot + nkeep) of the next round's list
-        unsigned slot = 0;
-        if (lane == 0 && nkeep) slot = atomicAdd(&rec->kept, nkeep);
-        slot = __shfl_sync(kFull, slot, 0);
 #pragma unroll
-        for (int u = 0; u < kHalf; ++u) {
-            if ((keepbits[u] >> lane) & 1u)
-                st_stream(io.rout + b + slot + __popc(keepbits[u] & ((1u << lane) - 1u)), w[u], io.pol_row);
-            slot += __popc(keepbits[u]);
+            for (int u = 0; u < kHalf; ++u) {
+                const int32_t j = sb + (int32_t)lane + 32 * (half * kHalf + u);
+                c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+            }
+            unsigned nkeep = 0;
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) {
+                const int32_t j = sb + (int32_t)lane + 32 * (half * kHalf + u);
+                const bool in = j < hi;
+                const uint32_t col = word_color(c[u]);
+                const bool settled = in && word_settled(c[u]);
+                if (in) {
+                    if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+                    m.set(col - 1u);
+                    if (settled) ms.set(col - 1u);
+                }
+                keepbits[u] = __ballot_sync(kFull, in && !settled);
+                nkeep += __popc(keepbits[u]);
+            }
+            // survivors go to [b + slot, b + slot + nkeep) of the next round's list
+            unsigned slot = local;
+            if (!single) {
+                if (lane == 0 && nkeep) slot = atomicAdd(&rec->kept, nkeep);
+                slot = __shfl_sync(kFull, slot, 0);
+            }
+            local += nkeep;
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) {
+                if ((keepbits[u] >> lane) & 1u)
+                    st_stream(io.rout + b + slot + __popc(keepbits[u] & ((1u << lane) - 1u)), w[u], io.pol_row);
+                slot += __popc(keepbits[u]);
+            }
         }
     }
     const bool any_conflict = __any_sync(kFull, conflict);
     const uint32_t word = m.warp_reduce_word();
     const uint32_t sword = ms.warp_reduce_word();
-    if (lane < 8u && word) atomicOr(&rec->mask[lane], word);
-    if (lane < 8u && sword) atomicOr(&rec->stat[lane], sword);
-    if (lane == 0 && any_conflict) atomicOr(&rec->conflict, 1u);
-    __threadfence();
-    const unsigned nch = (unsigned)(len + kChunk - 1) / kChunk;
-    unsigned done = 0;
-    if (lane == 0) done = atomicAdd(&rec->done, 1u);
-    done = __shfl_sync(kFull, done, 0);
-    if (done != nch - 1) return;
-    // last chunk of v: decide
-    __threadfence();
-    const bool conf = __ldcg(&rec->conflict) != 0u;
-    const int32_t kept = (int32_t)__ldcg(&rec->kept);
+    bool conf;
+    int32_t kept;
     uint32_t all = 0, stat = 0;
-    if (lane < 8u) {
-        const uint32_t old = io.first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
-        stat = old | __ldcg(&rec->stat[lane]);
-        all = stat | __ldcg(&rec->mask[lane]);
+    if (single) {
+        conf = any_conflict;
+        kept = (int32_t)local;
+        if (lane < 8u) {
+            const uint32_t old = io.first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
+            stat = old | sword;
+            all = stat | word;
+        }
+    } else {
+        if (lane < 8u && word) atomicOr(&rec->mask[lane], word);
+        if (lane < 8u && sword) atomicOr(&rec->stat[lane], sword);
+        if (lane == 0 && any_conflict) atomicOr(&rec->conflict, 1u);
+        __threadfence();
+        unsigned done = 0;
+        if (lane == 0) done = atomicAdd(&rec->done, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != nch - 1) return;
+        // last chunk of v: decide
+        __threadfence();
+        conf = __ldcg(&rec->conflict) != 0u;
+        kept = (int32_t)__ldcg(&rec->kept);
+        if (lane < 8u) {
+            const uint32_t old = io.first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
+            stat = old | __ldcg(&rec->stat[lane]);
+            all = stat | __ldcg(&rec->mask[lane]);
+        }
+        ((unsigned*)rec)[lane] = 0u;  // reset for the next round (32 words)
     }
-    ((unsigned*)rec)[lane] = 0u;  // reset for the next round (32 words)
     if (!conf) {
         if (lane == 0) settle(p, io, v, cv);
         maxc = max(maxc, (int)cv);
@@ -961,7 +1015,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
 // separates the rounds.  Every block reads the same counts and status after
 // a barrier, so all blocks leave the loop in the same round.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) rounds_persistent_kernel(Params<T> p) {
+__global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
     for (int k = 2;; ++k) {
@@ -994,7 +1048,7 @@ __global__ void __launch_bounds__(256, 4) rounds_persistent_kernel(Params<T> p) 
 
 // One pass per launch (loop mode 1): counts come from the host.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
+__global__ void __launch_bounds__(256, kMinBlocks) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
                                                        unsigned nHC) {
     int maxc = 0;
     run_pass(p, k, nS, nM, nHC, maxc);
