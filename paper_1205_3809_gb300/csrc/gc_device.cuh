@@ -868,7 +868,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
 // warp that completes the last chunk decides it and clears the record.
 template <typename T>
 __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
-                                          int& maxc, unsigned& vol) {
+                                          FlatSmem& sm, int& maxc, unsigned& vol) {
     constexpr int kHalf = kPerLane / 2;
     const unsigned lane = lane_id();
     const int32_t v = h.e.x, b = h.e.y, len = h.e.z;
@@ -879,9 +879,9 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
     bool conflict = false;
-    Mask256 m, ms;
-    m.clear();
-    ms.clear();
+    // this chunk's color windows: all colors in sm.dyn[0..8), settled ones in sm.stat[0..8)
+    if (lane < 8u) { sm.dyn[lane] = 0u; sm.stat[lane] = 0u; }
+    __syncwarp();
     HubRecord* rec = p.hubs + h.pos;
     unsigned local = 0;  // survivors written so far (single-chunk vertex)
     for (int32_t sb = lo; sb < hi; sb += kHubSub) {
@@ -909,8 +909,12 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
                 const bool settled = in && word_settled(c[u]);
                 if (in) {
                     if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
-                    m.set(col - 1u);
-                    if (settled) ms.set(col - 1u);
+                    const unsigned idx = col - 1u;
+                    if (idx < 256u) {
+                        const uint32_t bit = 1u << (idx & 31u);
+                        atomicOr(&sm.dyn[idx >> 5], bit);
+                        if (settled) atomicOr(&sm.stat[idx >> 5], bit);
+                    }
                 }
                 keepbits[u] = __ballot_sync(kFull, in && !settled);
                 nkeep += __popc(keepbits[u]);
@@ -931,8 +935,10 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
         }
     }
     const bool any_conflict = __any_sync(kFull, conflict);
-    const uint32_t word = m.warp_reduce_word();
-    const uint32_t sword = ms.warp_reduce_word();
+    __syncwarp();
+    const uint32_t word = sm.dyn[lane & 7u];
+    const uint32_t sword = sm.stat[lane & 7u];
+    __syncwarp();
     bool conf;
     int32_t kept;
     uint32_t all = 0, stat = 0;
@@ -1002,7 +1008,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         TaskHead nxt;
         if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM);
         if (t < nHC) {
-            hub_chunk(p, io, cur, maxc, vol);
+            hub_chunk(p, io, cur, s_flat[wib], maxc, vol);
         } else {
             flat_task(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_flat[wib], maxc, vol);
         }
