@@ -50,7 +50,8 @@ typedef enum gc_status {
     GC_ERR_OOM = -3,        /* workspace allocation failed */
     GC_ERR_MAX_ROUNDS = -4, /* U not empty after max_rounds rounds */
     GC_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
-    GC_ERR_BAD_GRAPH = -6   /* CSR rejected by the setup scan or validation */
+    GC_ERR_BAD_GRAPH = -6,  /* CSR rejected by the setup scan or validation */
+    GC_ERR_TOO_LARGE = -7   /* gc_color_noalloc: graph needs more scratch than it has */
 } gc_status;
 
 /*
@@ -166,6 +167,38 @@ size_t gc_workspace_bytes(void);
 /* Number of kernel launches made by the last successful call on this
  * process (for launch accounting). */
 int64_t gc_last_launch_count(void);
+
+/*
+ * gc_color_noalloc - gc_color for callers that cannot allocate memory while
+ * they run: for example inside a framework whose caching allocator has
+ * already reserved the device's memory, in a service with a fixed memory
+ * plan that allocates nothing after start-up, or where cudaMalloc / cudaFree
+ * must not synchronise the device.  The paper has no counterpart; this is an
+ * interface of this library only.
+ *
+ * Same arguments and results as gc_color (device inputs and colors_out,
+ * host ncolors and rounds, index priority when priority is NULL), on
+ * `stream` (a cudaStream_t, NULL = legacy default stream), always with the
+ * default options.  It calls no cudaMalloc, cudaMallocHost, cudaFree or any
+ * other allocating routine: its workspace is one file-scope device array of
+ * gc_noalloc_capacity_bytes() bytes (64 MiB), which every GPU that loads the
+ * library holds until the process exits, and its host staging is on the
+ * stack.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and it keeps the last call's
+ * contents; each call clears what must start at zero, but calls that overlap
+ * on the GPU (on different streams) race on it and must not be issued.
+ * Calls from several host threads are serialised.
+ * Returns GC_ERR_TOO_LARGE when the graph needs more workspace than the
+ * array holds (roughly 70 bytes per vertex plus 8 per adjacency entry), and
+ * otherwise the codes gc_color returns.
+ */
+int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n,
+                     const uint32_t* priority, int32_t* colors_out, int32_t* ncolors,
+                     int32_t* rounds, void* stream);
+
+/* Size in bytes of the fixed workspace gc_color_noalloc uses. */
+size_t gc_noalloc_capacity_bytes(void);
 
 #ifdef __cplusplus
 }

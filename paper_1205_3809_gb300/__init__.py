@@ -30,11 +30,12 @@ GC_ERR_OOM = -3
 GC_ERR_MAX_ROUNDS = -4
 GC_ERR_TIMEOUT = -5
 GC_ERR_BAD_GRAPH = -6
+GC_ERR_TOO_LARGE = -7
 
 # Every symbol include/gc.h declares.
 EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_strerror",
             "gc_last_cuda_error", "gc_release", "gc_workspace_bytes", "gc_last_launch_count",
-            "gc_last_round_stats", "gc_last_phase_ms")
+            "gc_last_round_stats", "gc_last_phase_ms", "gc_color_noalloc", "gc_noalloc_capacity_bytes")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -102,6 +103,9 @@ def _load():
         lib.gc_workspace_bytes.restype = ctypes.c_size_t
         lib.gc_last_launch_count.restype = ctypes.c_int64
         lib.gc_last_round_stats.argtypes = [vp, vp, i32]
+        lib.gc_color_noalloc.argtypes = [vp, vp, i32, vp, vp, i32p, i32p, vp]
+        lib.gc_color_noalloc.restype = ctypes.c_int
+        lib.gc_noalloc_capacity_bytes.restype = ctypes.c_size_t
         lib.gc_last_phase_ms.argtypes = [vp, i32]
         for f in (lib.gc_color, lib.gc_color_ex, lib.gc_color_host, lib.gc_validate_csr,
                   lib.gc_last_cuda_error, lib.gc_release, lib.gc_last_round_stats,

@@ -432,6 +432,157 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     return GC_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Coloring without any allocation (gc_color_noalloc).
+//
+// Some callers cannot allocate device memory while they run: a framework
+// whose caching allocator has already reserved the device's memory, a
+// service with a fixed memory plan that allocates nothing after start-up,
+// or a caller that must not let cudaMalloc / cudaFree synchronise the
+// device.  For them the workspace lives in this file-scope device array,
+// which every GPU that loads the library holds until the process exits.
+// The array's name is only a host-side stand-in for the device object, so
+// its device address is fetched once per device with cudaGetSymbolAddress
+// (that happens on the first call on each device).  Every call shares the
+// array and the array keeps the last call's contents: everything that must
+// start at zero is cleared on the call's stream, and calls that overlap on
+// the GPU (two streams, or two host threads on different streams) would
+// race on it.  Host staging uses stack memory, never pinned allocations.
+constexpr size_t kNoAllocBytes = 64ull << 20;  // 64 MiB
+constexpr int kNoAllocMaxDevices = 64;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    int ready = 0;
+    int sms = 0;
+    int coop = 0;
+    void* scratch = nullptr;  // device address of g_noalloc_scratch on that device
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+int noalloc_device(NoAllocDevice** out) {
+    int dev = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GC_ERR_INVALID;
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        GC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        GC_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        GC_CUDA(cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, dev));
+        d.scratch = ptr;
+        d.ready = 1;
+    }
+    *out = &d;
+    return GC_OK;
+}
+
+int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n,
+                         const uint32_t* priority, int32_t* colors_out, int32_t* ncolors,
+                         int32_t* rounds, cudaStream_t s) {
+    if (n < 0 || !ncolors || !rounds) return GC_ERR_INVALID;
+    if (n > 0 && (!rowptr || !colors_out)) return GC_ERR_INVALID;
+    if (n == 0) {
+        *ncolors = 0;
+        *rounds = 0;
+        return GC_OK;
+    }
+    gc_options o;
+    int rc = normalise(nullptr, &o);
+    if (rc != GC_OK) return rc;
+    NoAllocDevice* nd = nullptr;
+    rc = noalloc_device(&nd);
+    if (rc != GC_OK) return rc;
+    char* base = (char*)nd->scratch;
+
+    // setup scan, its record at the start of the scratch array
+    Stats hs;
+    {
+        Stats* stats = (Stats*)base;
+        GC_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), s));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)nd->sms * 8));
+        gc::stats_kernel<<<grid, 256, 0, s>>>(rowptr, n, o.small_max_degree, o.medium_max_degree, stats);
+        GC_CUDA(cudaGetLastError());
+        GC_CUDA(cudaMemcpyAsync(&hs, stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (hs.bad || hs.nnz < 0) return GC_ERR_BAD_GRAPH;
+    if (hs.nnz > 0 && !colidx) return GC_ERR_INVALID;
+
+    DeviceCache dc;  // only the device attributes run_rounds reads; nothing is allocated
+    dc.sms = nd->sms;
+    dc.coop = nd->coop;
+    const int64_t round_cap = 1;  // no per-round telemetry
+    int bits = 16;
+    RoundState* st = nullptr;
+    for (;;) {
+        const size_t elem = bits == 16 ? 2 : 4;
+        const Layout L = make_layout(n, hs.nnz, elem, hs, round_cap);
+        if (L.total > kNoAllocBytes) return GC_ERR_TOO_LARGE;
+        st = (RoundState*)(base + L.st);
+        GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
+        GC_CUDA(cudaMemsetAsync(base + L.rv, 0, (size_t)round_cap * sizeof(unsigned long long), s));
+        GC_CUDA(cudaMemsetAsync(base + L.hubs, 0, (size_t)hs.cap[gc::kBinH] * sizeof(gc::HubRecord), s));
+        auto fill = [&](auto& p) {
+            using PT = std::remove_reference_t<decltype(p)>;
+            using T = std::remove_pointer_t<decltype(PT::X0)>;
+            p.rowptr = rowptr;
+            p.colidx = colidx;
+            p.prio = priority;
+            p.n = n;
+            p.s_max = o.small_max_degree;
+            p.m_max = o.medium_max_degree;
+            p.max_rounds = n;
+            p.color_limit = bits == 16 ? 0x8000u : 0x80000000u;
+            p.X0 = (T*)(base + L.x0);
+            p.X1 = (T*)(base + L.x1);
+            p.colors_out = colors_out;
+            p.act0 = (int32_t*)(base + L.act0);
+            p.act1 = (int32_t*)(base + L.act1);
+            p.stat = (uint32_t*)(base + L.stat);
+            p.SA = (int4*)(base + L.S[0]);
+            p.MA = (int4*)(base + L.M[0]);
+            p.HA = (int4*)(base + L.H[0]);
+            p.HcA = (int32_t*)(base + L.Hc[0]);
+            p.OA = (int32_t*)(base + L.O[0]);
+            p.SB = (int4*)(base + L.S[1]);
+            p.MB = (int4*)(base + L.M[1]);
+            p.HB = (int4*)(base + L.H[1]);
+            p.HcB = (int32_t*)(base + L.Hc[1]);
+            p.OB = (int32_t*)(base + L.O[1]);
+            p.defer = (int32_t*)(base + L.defer);
+            p.hubs = (gc::HubRecord*)(base + L.hubs);
+            p.st = st;
+            p.round_sizes = (int32_t*)(base + L.rs);
+            p.round_vol = (unsigned long long*)(base + L.rv);
+            p.round_cap = (int32_t)round_cap;
+        };
+        int64_t launches = 0;
+        if (bits == 16) {
+            Params<uint16_t> p;
+            fill(p);
+            rc = run_rounds(o, dc, p, s, &launches);
+        } else {
+            Params<int32_t> p;
+            fill(p);
+            rc = run_rounds(o, dc, p, s, &launches);
+        }
+        if (rc != GC_OK) return rc;
+        RoundState hst;
+        GC_CUDA(cudaMemcpyAsync(&hst, st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (bits == 16 && hst.status == gc::kStatusColorOverflow) {
+            bits = 32;
+            continue;
+        }
+        if (hst.status == gc::kStatusTimeout) return GC_ERR_TIMEOUT;
+        if (hst.status == gc::kStatusMaxRounds) return GC_ERR_MAX_ROUNDS;
+        *rounds = hst.rounds;
+        *ncolors = hst.max_color;
+        return GC_OK;
+    }
+}
 }  // namespace
 
 extern "C" {
@@ -513,6 +664,7 @@ const char* gc_strerror(int code) {
         case GC_ERR_MAX_ROUNDS: return "worklist not empty after max_rounds rounds";
         case GC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case GC_ERR_BAD_GRAPH: return "graph rejected (CSR shape, index range, self loop or asymmetry)";
+        case GC_ERR_TOO_LARGE: return "graph needs more scratch memory than gc_color_noalloc's fixed buffer holds";
         default: return "unknown gc_status";
     }
 }
@@ -574,5 +726,15 @@ size_t gc_workspace_bytes(void) {
 }
 
 int64_t gc_last_launch_count(void) { return g_last_launches; }
+
+int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                     int32_t* colors_out, int32_t* ncolors, int32_t* rounds, void* stream) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_last_cuda_error = 0;
+    return color_noalloc_locked(rowptr, colidx, n, priority, colors_out, ncolors, rounds,
+                                (cudaStream_t)stream);
+}
+
+size_t gc_noalloc_capacity_bytes(void) { return kNoAllocBytes; }
 
 }  // extern "C"
