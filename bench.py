@@ -40,6 +40,10 @@ SCALE, EF, ABCD, SEED = 24, 8, gg.RMAT_B, 3
 CPU_BASELINE_SCALE = 22
 REFERENCE_STEP_SCALE = 20
 
+# Random 16-bit gathers from an L2-resident table, driven by a streamed int32
+# index array, measured on this machine's GB300 (profiles/l2_random_gather.md).
+L2_GATHER_CEILING = 215.0  # G gathers/s
+
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -153,19 +157,30 @@ def run_reference(args):
 # ----------------------------------------------------------- roofline bits
 
 def algorithmic_bytes_rounds(sizes, vols, elem):
-    """Bytes the fused passes k >= 2 must move (one launch of the rounds kernel).
+    """Bytes one launch of the rounds kernel must move (rounds k >= 2).
 
-    Per pass over W = U_k: list 4|W| + rowptr pair 8|W| + own color elem|W|
-    + vol(W) * (4 colidx + elem neighbour color) + writes: next color elem|W|
-    + final int32 color 4 per settled vertex + list append 4|U_{k+1}|.
+    sizes[k-1] = |U_k|, vols[k-1] = A_k, the active-list entries round k reads
+    (A_2 = full rows; later rounds read only neighbours not yet settled).
+    Per round k: active list 4*A_k + neighbour colors elem*A_k + worklist
+    tuples 16|U_k| + own color elem|U_k| + static masks 32|U_k| (k >= 3);
+    writes: survivors 4*A_{k+1}, next tuples 16|U_{k+1}|, static masks
+    32|U_{k+1}|, next color elem|U_k|, final int32 color 4 per settled vertex.
     """
     total = 0
     R = len(sizes)
     for k in range(2, R + 1):
-        w, vol = int(sizes[k - 1]), int(vols[k - 1])
-        nxt = int(sizes[k]) if k < R else 0
-        total += 4 * w + 8 * w + elem * w + vol * (4 + elem) + elem * w + 4 * (w - nxt) + 4 * nxt
+        u, a = int(sizes[k - 1]), int(vols[k - 1])
+        un = int(sizes[k]) if k < R else 0
+        an = int(vols[k]) if k < R else 0
+        reads = 4 * a + elem * a + 16 * u + elem * u + (32 * u if k >= 3 else 0)
+        writes = 4 * an + 16 * un + 32 * un + elem * u + 4 * (u - un)
+        total += reads + writes
     return total
+
+
+def gathers_rounds(vols):
+    """Random neighbour-color reads of the rounds kernel (one per active entry)."""
+    return int(sum(int(x) for x in vols[1:]))
 
 
 def load_traffic(kernel_src):
@@ -213,7 +228,7 @@ def run_ours(args):
     gcpkg.library()
 
     t = time.time()
-    g = gg.rmat(SCALE, EF, ABCD, SEED)
+    g = gg.rmat(args.scale, EF, ABCD, SEED)
     log(f"[rank {rank}] graph n={g.n} m={g.m} maxdeg={g.max_degree} generated in {time.time() - t:.1f}s")
     rp = torch.from_numpy(g.rowptr).to(dev)
     ci = torch.from_numpy(g.colidx).to(dev)
@@ -263,12 +278,14 @@ def run_ours(args):
     value = world * args.steps * g.m / total_s
 
     sizes, vols = gcpkg.last_round_stats()
-    elem = 2 if g.max_degree + 1 <= 65535 else 4
+    elem = 2  # 16-bit color state (the library restarts with 32 bits only past 32767 colors)
     alg_bytes = algorithmic_bytes_rounds(sizes, vols, elem)
     kms = statistics.mean(kernel_ms)
     achieved = alg_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = load_traffic(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
+    gathers = gathers_rounds(vols)
+    gather_rate = gathers / (kms / 1e3) / 1e9
 
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
@@ -307,7 +324,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "ncolors": res.ncolors, "rounds": res.rounds,
-            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "max_degree": g.max_degree,
+            "config": {"workload": WORKLOAD if args.scale == SCALE else WORKLOAD.replace("scale 24", f"scale {args.scale}"),
+                       "n": g.n, "m": g.m, "max_degree": g.max_degree,
                        "priority": "index (plain)", "loop": "persistent cooperative launch",
                        "color_state_bits": 8 * elem,
                        "l2": "inputs larger than L2 (colidx 1.07 GB) and L2 flushed (256 MB write) "
@@ -316,7 +334,10 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "rounds_persistent_kernel",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic_bytes": alg_bytes, "kernel_ms": kms},
+                         "algorithmic_bytes": alg_bytes, "kernel_ms": kms,
+                         "l2_gathers": {"count": gathers, "achieved_G_per_s": gather_rate,
+                                        "ceiling_G_per_s": L2_GATHER_CEILING,
+                                        "frac": gather_rate / L2_GATHER_CEILING}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -327,6 +348,17 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def measure_l2_ceiling():
+    src = os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "l2_gather_probe.cu")
+    exe = os.path.join(ROOT, "gpurun_out", "l2_gather_probe")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    try:
+        subprocess.run([exe], check=True)
+    finally:
+        os.remove(exe)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,7 +367,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="R-MAT-B scale (24 is the benchmark; smaller scales are for profiling)")
+    ap.add_argument("--measure-l2-ceiling", action="store_true",
+                    help="build and run the random-gather ceiling probe, then exit")
     args = ap.parse_args()
+    if args.measure_l2_ceiling:
+        measure_l2_ceiling()
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
