@@ -80,7 +80,7 @@ class Graph:
 
     @property
     def m(self) -> int:
-        """Undirected edge count, as the paper counts edges (Table 1)."""
+        """Undirected edge count, as the paper counts edges (Table 2)."""
         return self.nnz // 2
 
     @property

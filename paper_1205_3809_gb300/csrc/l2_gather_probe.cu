@@ -24,7 +24,8 @@ __global__ void gather_global(const int* __restrict__ idx, const uint16_t* tab, 
         for (int u = 0; u < 4; ++u)
             if (w[u] >= 0) acc ^= cached ? __ldg(tab + w[u]) : __ldcg(tab + w[u]);
     }
-    if (acc == 0x12345678u) out[0] = acc;
+    // a condition the compiler cannot decide keeps the gathers alive
+    if (acc == (unsigned)m) out[0] = acc;
 }
 
 __global__ void gather_smem(const int* __restrict__ idx, const uint16_t* tab, int N, long long m,
@@ -45,7 +46,7 @@ __global__ void gather_smem(const int* __restrict__ idx, const uint16_t* tab, in
         for (int u = 0; u < 4; ++u)
             if (w[u] >= 0) acc ^= s[w[u] % N];
     }
-    if (acc == 0x12345678u) out[0] = acc;
+    if (acc == (unsigned)m) out[0] = acc;
 }
 
 int main() {

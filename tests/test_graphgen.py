@@ -1,5 +1,5 @@
 """The synthetic inputs: simple symmetric CSR, deterministic, and shaped like the
-paper's R-MAT test graphs (Sec. 4.1, Tables 1 and 5)."""
+paper's R-MAT test graphs (Sec. 4.1, Tables 2 and 4)."""
 import numpy as np
 import pytest
 
@@ -63,7 +63,7 @@ def test_rgg_average_degree():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("abcd,edges,maxdeg,var,isolated", [
-    # Table 5 (scale 24): edges, max degree, variance, % isolated vertices
+    # Table 4 (scale 24 rows): edges, max degree, variance, % isolated vertices
     (gg.RMAT_ER, 134217654, 42, 16.00, 0.0),
     (gg.RMAT_B, 133658229, 38143, 8085.64, 30.81),
 ])
