@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_LEARNED = os.path.join(_HERE, "learned.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORC_OK = 0
@@ -28,9 +29,10 @@ ORC_ERR_MAX_ROUNDS = -4
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so (single-threaded, -O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_LEARNED))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-Wall",
-               "-o", _LIB, _SRC, "-lm"]
+               "-o", _LIB, _SRC, _SRC_LEARNED, "-lm"]
         subprocess.run(cmd, check=True)
     return _LIB
 
@@ -51,8 +53,12 @@ def _load():
         lib.orc_chromatic_number.argtypes = [i32, vp, vp, vp]
         lib.orc_largest_first_order.argtypes = [i32, vp, vp]
         lib.orc_smallest_last_order.argtypes = [i32, vp, vp, vp, vp]
+        lib.orc_features.argtypes = [i32, vp, vp, vp]
+        lib.orc_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+        lib.orc_bf16_array.argtypes = [vp, ctypes.c_int64, vp]
         for f in (lib.orc_greedy, lib.orc_iterative, lib.orc_chromatic_number,
-                  lib.orc_largest_first_order, lib.orc_smallest_last_order):
+                  lib.orc_largest_first_order, lib.orc_smallest_last_order, lib.orc_features,
+                  lib.orc_mlp_forward, lib.orc_bf16_array, lib.orc_mlp_param_count):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
