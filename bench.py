@@ -287,6 +287,8 @@ def run_ours(args):
     gathers = gathers_rounds(vols)
     gather_rate = gathers / (kms / 1e3) / 1e9
 
+    learned = None if args.no_learned else measure_learned(gcpkg, rp, ci, g, flush, stream, args)
+
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
     if not args.no_e2e:
@@ -339,6 +341,7 @@ def run_ours(args):
                                         "ceiling_G_per_s": L2_GATHER_CEILING,
                                         "frac": gather_rate / L2_GATHER_CEILING}},
             "cpu_baseline": cpu,
+            "learned": learned,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -346,6 +349,57 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_learned(gcpkg, rp, ci, g, flush, stream, args):
+    """The learned-priority form on the same graph: features -> network -> keys ->
+    coloring under those keys, timed as one step with CUDA events on the
+    launching stream (L2 flushed before each step), phases split by events."""
+    import torch
+    if not os.path.exists(gcpkg.PRIORITY_MODEL):
+        return {"unavailable": "no trained model file"}
+    params = gcpkg.load_priority_model(device=rp.device)
+    n = g.n
+    feats = torch.empty((n, 6), dtype=torch.float32, device=rp.device)
+    scores = torch.empty(n, dtype=torch.float32, device=rp.device)
+    keys = torch.empty(n, dtype=torch.int32, device=rp.device)
+    lout = torch.empty(n, dtype=torch.int32, device=rp.device)
+
+    def step(ev=None):
+        gcpkg.features(rp, ci, out=feats, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        gcpkg.mlp_forward(params, feats, out=scores, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        gcpkg.priority_keys(scores, out=keys, stream=stream)
+        if ev:
+            ev[3].record(stream)
+        return gcpkg.color(rp, ci, keys, out=lout, stream=stream)
+
+    for _ in range(3):
+        flush.zero_()
+        res = step()
+    torch.cuda.synchronize()
+    k = max(5, args.steps // 3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(k)]
+    launches = 0
+    for i in range(k):
+        flush.zero_()
+        evs[i][0].record(stream)
+        res = step(evs[i])
+        evs[i][4].record(stream)
+        launches += 3 + gcpkg.last_launch_count()
+    torch.cuda.synchronize()
+    tot = [e[0].elapsed_time(e[4]) for e in evs]
+    phase = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j in range(4)]
+    ms = statistics.mean(tot)
+    return {"value": g.m / (ms / 1e3), "unit": "edges/s", "ms_per_step": ms, "steps": k,
+            "ncolors": res.ncolors, "rounds": res.rounds,
+            "phase_ms": {"features": phase[0], "mlp_forward": phase[1], "keys": phase[2],
+                         "coloring": phase[3]},
+            "model": os.path.basename(gcpkg.PRIORITY_MODEL) + " (trained on R-MAT-G scales 14-18)",
+            "gpu_launches": launches}
 
 
 def measure_l2_ceiling():
@@ -367,6 +421,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT-B scale (24 is the benchmark; smaller scales are for profiling)")
     ap.add_argument("--measure-l2-ceiling", action="store_true",

@@ -200,6 +200,56 @@ int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n,
 /* Size in bytes of the fixed workspace gc_color_noalloc uses. */
 size_t gc_noalloc_capacity_bytes(void);
 
+/*
+ * Learned priority.  The paper colors in index order (Sec. 3.2) and cites
+ * vertex-ordering heuristics for Algorithm 1 (smallest-last, largest-first;
+ * Sec. 1, Sec. 3.1).  These entry points compute per-vertex features, run a
+ * small MLP that scores where a vertex would sit in such an ordering, and turn
+ * scores into gc_color priority keys.  All arrays are device arrays owned by
+ * the caller; calls are asynchronous on `stream` and return after launching.
+ * They return GC_OK, GC_ERR_INVALID or GC_ERR_CUDA.
+ */
+
+/* gc_features - features[6*v .. 6*v+5] of vertex v (fp32), deg = degree of v,
+ * nbr = degrees of v's neighbours: log2(1+deg), floor(log2(1+deg)),
+ * log2(1+mean nbr), log2(1+max nbr), log2(1+sum nbr), log2(1+min nbr)
+ * (the last four 0 for an isolated vertex).  Graph as for gc_color. */
+int gc_features(const int32_t* rowptr, const int32_t* colidx, int32_t n, float* features, void* stream);
+
+/* Number of MLP parameters (1313): fp32 vector W1[32][6] | b1[32] |
+ * W2[32][32] | b2[32] | W3[32] | b3.  Forward of features x: a0 = bf16(x),
+ * a1 = bf16(relu(bf16(W1) a0 + b1)), a2 = bf16(relu(bf16(W2) a1 + b2)),
+ * y = bf16(W3) . a2 + b3; products accumulate in fp32, bf16 rounds to
+ * nearest even. */
+int gc_mlp_param_count(void);
+
+/* gc_mlp_forward - y[i] = MLP(x[6*i .. 6*i+5]) for i < n. */
+int gc_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream);
+
+/* gc_mlp_grad - adds the gradient of scale * sum_i (y_i - t_i)^2 with respect
+ * to params into grad (1313 floats) and sum_i (y_i - t_i)^2 into *sse
+ * (device scalar).  Both accumulate: zero them first. */
+int gc_mlp_grad(const float* params, const float* x, const float* t, int64_t n, float scale, float* grad,
+                float* sse, void* stream);
+
+/* gc_mlp_adam - one Adam step (Kingma & Ba) on params with moments m, v
+ * (1313 floats each, zero before step 1); step counts from 1. */
+int gc_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t step, float lr, float beta1,
+                float beta2, float eps, void* stream);
+
+/* gc_mlp_train_step - one training step on the mean squared error of n
+ * samples: zeroes grad (1313 floats) and *sse, adds the gradient of
+ * (1/n) sum_i (y_i - t_i)^2 (gc_mlp_grad with scale 1/n), then takes
+ * gc_mlp_adam step `step`.  Afterwards *sse holds sum_i (y_i - t_i)^2 under
+ * the parameters before the update. */
+int gc_mlp_train_step(float* params, float* m, float* v, float* grad, float* sse, const float* x, const float* t,
+                      int64_t n, int32_t step, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* gc_priority_keys - keys[i] = a uint32 with the order of scores[i] (smaller
+ * score, smaller key, higher precedence; -0 = +0; NaN last).  Equal scores
+ * give equal keys, and gc_color then breaks the tie by index. */
+int gc_priority_keys(const float* scores, int64_t n, uint32_t* keys, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

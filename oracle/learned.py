@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle``: the library never imports
 it.  The paper colors in index order (Sec. 3.2) and cites vertex orderings for
 Greedy (smallest-last, largest-first: Sec. 1, Sec. 3.1); the learned priority
 replaces the index by a key that a small network computes from per-vertex
-features, trained to place each vertex where the smallest-last ordering puts it.
+features, trained to place each vertex where the smallest-last ordering puts it
+(on a log scale of the position).
 
 ``features`` and ``mlp_forward`` wrap ``learned.c`` (the score decides the order
 of the keys, so it is computed in the network's own precision: bf16 operands,
@@ -144,10 +145,15 @@ def learned_keys(rowptr, colidx, params) -> np.ndarray:
 
 
 def smallest_last_targets(rowptr, colidx) -> np.ndarray:
-    """Training target of each vertex: its position in the smallest-last ordering
-    divided by n (0 = colored first), float32 [n]."""
+    """Training target of each vertex: log2(1 + its position in the smallest-last
+    ordering), position 0 = colored first; float32 [n].
+
+    The log spreads the front of the ordering (the dense core, which decides the
+    number of colors) over as wide a range as the rest, and keeps the target of
+    the first vertices the same in graphs of any size.
+    """
     order, _ = smallest_last_order(rowptr, colidx)
     n = order.shape[0]
     pos = np.empty(n, np.float64)
     pos[order] = np.arange(n, dtype=np.float64)
-    return (pos / max(n, 1)).astype(np.float32)
+    return np.log2(1.0 + pos).astype(np.float32)

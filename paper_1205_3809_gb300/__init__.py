@@ -35,7 +35,9 @@ GC_ERR_TOO_LARGE = -7
 # Every symbol include/gc.h declares.
 EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_strerror",
             "gc_last_cuda_error", "gc_release", "gc_workspace_bytes", "gc_last_launch_count",
-            "gc_last_round_stats", "gc_last_phase_ms", "gc_color_noalloc", "gc_noalloc_capacity_bytes")
+            "gc_last_round_stats", "gc_last_phase_ms", "gc_color_noalloc", "gc_noalloc_capacity_bytes",
+            "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
+            "gc_priority_keys", "gc_mlp_train_step")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -63,8 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             and all(os.path.getmtime(LIB_PATH) >= os.path.getmtime(s) for s in srcs)):
         return LIB_PATH
     cmd = ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "-I", _INCLUDE, "-o", LIB_PATH + ".tmp",
-           os.path.join(_CSRC, "gc.cu")]
+           "-Xcompiler", "-fPIC", "-shared", "-I", _INCLUDE, "--threads", "2", "-o", LIB_PATH + ".tmp",
+           os.path.join(_CSRC, "gc.cu"), os.path.join(_CSRC, "gc_mlp.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)
@@ -106,6 +108,17 @@ def _load():
         lib.gc_color_noalloc.argtypes = [vp, vp, i32, vp, vp, i32p, i32p, vp]
         lib.gc_color_noalloc.restype = ctypes.c_int
         lib.gc_noalloc_capacity_bytes.restype = ctypes.c_size_t
+        i64, f32 = ctypes.c_int64, ctypes.c_float
+        lib.gc_features.argtypes = [vp, vp, i32, vp, vp]
+        lib.gc_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        lib.gc_mlp_grad.argtypes = [vp, vp, vp, i64, f32, vp, vp, vp]
+        lib.gc_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]
+        lib.gc_priority_keys.argtypes = [vp, i64, vp, vp]
+        lib.gc_mlp_train_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i32, f32, f32, f32, f32, vp]
+        lib.gc_mlp_train_step.restype = ctypes.c_int
+        for f in (lib.gc_features, lib.gc_mlp_forward, lib.gc_mlp_grad, lib.gc_mlp_adam,
+                  lib.gc_priority_keys, lib.gc_mlp_param_count):
+            f.restype = ctypes.c_int
         lib.gc_last_phase_ms.argtypes = [vp, i32]
         for f in (lib.gc_color, lib.gc_color_ex, lib.gc_color_host, lib.gc_validate_csr,
                   lib.gc_last_cuda_error, lib.gc_release, lib.gc_last_round_stats,
@@ -282,3 +295,154 @@ def last_phase_ms():
     if m < 0:
         raise GcError(m, "gc_last_phase_ms")
     return [float(ms[i]) for i in range(m)]
+
+
+# ---------------------------------------------------------------- learned priority
+
+MLP_PARAMS = 1313
+PRIORITY_MODEL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "priority_mlp_rmat_g.json")
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != GC_OK:
+        raise GcError(rc, what, _load().gc_last_cuda_error())
+
+
+def features(rowptr, colidx, *, out=None, stream=None):
+    """float32 [n, 6] per-vertex features of a graph held on the GPU (``gc_features``)."""
+    import torch
+    lib = _load()
+    n = int(rowptr.numel()) - 1
+    rp = _dev_ptr(rowptr, torch.int32, "rowptr", None)
+    ci = _dev_ptr(colidx, torch.int32, "colidx", None)
+    if out is None:
+        out = torch.empty((max(n, 0), 6), dtype=torch.float32, device=rowptr.device)
+    fo = _dev_ptr(out, torch.float32, "out", max(n, 0) * 6)
+    with torch.cuda.device(rowptr.device):
+        _check(lib.gc_features(rp, ci, n, fo, _stream_handle(stream, rowptr.device)), "gc_features")
+    return out
+
+
+def mlp_forward(params, x, *, out=None, stream=None):
+    """Network scores, float32 [n], of features x (float32 [n, 6]) (``gc_mlp_forward``)."""
+    import torch
+    lib = _load()
+    n = int(x.numel()) // 6
+    pp = _dev_ptr(params, torch.float32, "params", MLP_PARAMS)
+    xp = _dev_ptr(x, torch.float32, "x", n * 6)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+    yp = _dev_ptr(out, torch.float32, "out", n)
+    with torch.cuda.device(x.device):
+        _check(lib.gc_mlp_forward(pp, xp, n, yp, _stream_handle(stream, x.device)), "gc_mlp_forward")
+    return out
+
+
+def mlp_grad(params, x, t, scale: float, grad, sse, *, stream=None):
+    """Add the gradient of scale * sum (y - t)^2 into grad (float32 [1313]) and the sum of
+    squared errors into sse (float32 [1]) (``gc_mlp_grad``)."""
+    import torch
+    lib = _load()
+    n = int(t.numel())
+    args = (_dev_ptr(params, torch.float32, "params", MLP_PARAMS), _dev_ptr(x, torch.float32, "x", n * 6),
+            _dev_ptr(t, torch.float32, "t", n), n, float(scale),
+            _dev_ptr(grad, torch.float32, "grad", MLP_PARAMS), _dev_ptr(sse, torch.float32, "sse", 1))
+    with torch.cuda.device(x.device):
+        _check(lib.gc_mlp_grad(*args, _stream_handle(stream, x.device)), "gc_mlp_grad")
+
+
+def adam_step(params, m, v, grad, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, *, stream=None):
+    """One Adam step on params with moments m, v (all float32 [1313]) (``gc_mlp_adam``)."""
+    import torch
+    lib = _load()
+    ptrs = [_dev_ptr(a, torch.float32, name, MLP_PARAMS)
+            for a, name in ((params, "params"), (m, "m"), (v, "v"), (grad, "grad"))]
+    with torch.cuda.device(params.device):
+        _check(lib.gc_mlp_adam(*ptrs, int(step), float(lr), float(beta1), float(beta2), float(eps),
+                               _stream_handle(stream, params.device)), "gc_mlp_adam")
+
+
+class MlpTrainer:
+    """Adam training of the priority network on the GPU (``gc_mlp_train_step``).
+
+    Holds the parameters, both moments and the gradient as float32 CUDA tensors;
+    ``step(x, t)`` takes one step on the mean squared error of the batch and
+    returns its sum of squared errors as a device scalar (no host sync).
+    """
+
+    def __init__(self, params, lr: float = 3e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        import torch
+        self.params = params.detach().to(torch.float32).contiguous().clone()
+        dev = self.params.device
+        self.m = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+        self.v = torch.zeros_like(self.m)
+        self.grad = torch.zeros_like(self.m)
+        self.sse = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.lr, self.beta1, self.beta2, self.eps = lr, beta1, beta2, eps
+        self.t = 0
+
+    def step(self, x, t, stream=None):
+        import torch
+        lib = _load()
+        n = int(t.numel())
+        self.t += 1
+        ptrs = [_dev_ptr(a, torch.float32, name, MLP_PARAMS)
+                for a, name in ((self.params, "params"), (self.m, "m"), (self.v, "v"), (self.grad, "grad"))]
+        with torch.cuda.device(self.params.device):
+            _check(lib.gc_mlp_train_step(*ptrs, _dev_ptr(self.sse, torch.float32, "sse", 1),
+                                         _dev_ptr(x, torch.float32, "x", n * 6),
+                                         _dev_ptr(t, torch.float32, "t", n), n, self.t, float(self.lr),
+                                         float(self.beta1), float(self.beta2), float(self.eps),
+                                         _stream_handle(stream, self.params.device)), "gc_mlp_train_step")
+        return self.sse
+
+
+def priority_keys(scores, *, out=None, stream=None):
+    """uint32 keys (as int32) in the order of float32 scores (``gc_priority_keys``)."""
+    import torch
+    lib = _load()
+    n = int(scores.numel())
+    sp = _dev_ptr(scores, torch.float32, "scores", n)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=scores.device)
+    kp = _dev_ptr(out, torch.int32, "out", n)
+    with torch.cuda.device(scores.device):
+        _check(lib.gc_priority_keys(sp, n, kp, _stream_handle(stream, scores.device)), "gc_priority_keys")
+    return out
+
+
+def load_priority_model(path: Optional[str] = None, device=None):
+    """The trained network's float32 parameter vector (on ``device`` if given, else a numpy array)."""
+    import json
+    with open(path or PRIORITY_MODEL) as f:
+        doc = json.load(f)
+    p = np.asarray(doc["params"], dtype=np.float32)
+    if p.shape != (MLP_PARAMS,):
+        raise ValueError(f"model has {p.shape} parameters, expected {MLP_PARAMS}")
+    if device is None:
+        return p
+    import torch
+    return torch.from_numpy(p).to(device)
+
+
+def learned_priority(rowptr, colidx, params, *, stream=None):
+    """Priority keys of every vertex: keys(network(features)), all on the GPU."""
+    f = features(rowptr, colidx, stream=stream)
+    return priority_keys(mlp_forward(params, f, stream=stream), stream=stream)
+
+
+def color_learned(rowptr, colidx, params=None, *, options=None, stream=None, round_sizes=False) -> Result:
+    """Color with the learned priority (the trained model when params is None)."""
+    if params is None:
+        params = load_priority_model(device=rowptr.device)
+    keys = learned_priority(rowptr, colidx, params, stream=stream)
+    return color(rowptr, colidx, keys, options=options, stream=stream, round_sizes=round_sizes)

@@ -264,12 +264,14 @@ def test_keys_follow_score_order():
     assert k[0] == k[1] and k[4] == k[2]
 
 
-def test_smallest_last_targets_are_positions():
+def test_smallest_last_targets_are_log_positions():
     g = gg.rmat(10, 8, gg.RMAT_G, 2)
     t = L.smallest_last_targets(g.rowptr, g.colidx)
     order, _ = oracle.smallest_last_order(g.rowptr, g.colidx)
-    assert np.array_equal(np.sort(t * g.n).round().astype(np.int64), np.arange(g.n))
-    assert t[order[0]] == 0.0 and t[order[-1]] == np.float32((g.n - 1) / g.n)
+    pos = np.exp2(t.astype(np.float64)) - 1.0
+    assert np.array_equal(np.sort(pos.round().astype(np.int64)), np.arange(g.n))
+    assert np.allclose(pos[order], np.arange(g.n), rtol=1e-6, atol=1e-6)
+    assert t[order[0]] == 0.0 and t[order[1]] == 1.0 and t[order[3]] == 2.0
 
 
 def test_learned_keys_compose():
