@@ -197,3 +197,37 @@ def edgeless(n: int) -> Graph:
 
 def num_threads() -> int:
     return int(_load().gg_num_threads())
+
+
+# ---- the batched workload: many small graphs of mixed families
+
+BATCH_FAMILIES = ("grid2d", "rgg", "rmat_g")
+
+
+def batch_mix(count: int, seed: int, n_min: int = 1000, n_max: int = 200000):
+    """`count` graphs with sizes log-uniform in [n_min, n_max], families in turn
+    drawn from 2-D 5-point grids (rows x cols about n), random geometric graphs
+    (average degree 8) and R-MAT-G (edge factor 8; 2^round(log2 n) vertices,
+    since R-MAT's recursive quadrants define a power of two).  Graph i uses
+    SplitMix64 streams (seed, 41..43) at counter i."""
+    u = draws(seed, 41, count)
+    fam = draws(seed, 42, count)
+    gseed = draws(seed, 43, count)
+    lo, hi = np.log(float(n_min)), np.log(float(n_max))
+    out = []
+    for i in range(count):
+        x = float(u[i] >> np.uint64(11)) / float(1 << 53)
+        n = int(round(np.exp(lo + x * (hi - lo))))
+        s = int(gseed[i] & np.uint64(0x7FFFFFFF))
+        kind = BATCH_FAMILIES[int(fam[i] % np.uint64(3))]
+        if n < 2:
+            g = edgeless(max(n, 0))
+        elif kind == "grid2d":
+            rows = max(1, int(round(np.sqrt(n))))
+            g = grid2d(rows, max(1, int(round(n / rows))), s)
+        elif kind == "rgg":
+            g = rgg(n, s)
+        else:
+            g = rmat(max(1, int(round(np.log2(n)))), 8, RMAT_G, s)
+        out.append(g)
+    return out

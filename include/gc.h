@@ -201,6 +201,92 @@ int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n,
 size_t gc_noalloc_capacity_bytes(void);
 
 /*
+ * Batched coloring: many independent graphs in one persistent launch.
+ *
+ * Algorithm 2 (Sec. 3.2) in synchronous rounds on each graph of a batch, all
+ * graphs advancing together in one cooperative launch.  The batch is colored
+ * as the disjoint union of its graphs (vertex i of graph g = union vertex
+ * voff[g] + i, which keeps the order of indices inside every graph), so each
+ * graph gets exactly the colors, color count and round count that gc_color
+ * gives it alone.
+ *
+ * Input layout (device arrays owned by the caller), for G graphs:
+ *   vertex_offsets[G+1], edge_offsets[G+1] (HOST int64 arrays): graph g has
+ *     n_g = voff[g+1] - voff[g] vertices and nnz_g = eoff[g+1] - eoff[g]
+ *     adjacency entries; voff[0] = eoff[0] = 0, both nondecreasing,
+ *     voff[G] < 2^31 and eoff[G] < 2^31;
+ *   rowptr_cat[voff[G] + G]: graph g's own rowptr (n_g + 1 entries, from 0 to
+ *     nnz_g) at rowptr_cat[voff[g] + g ..];
+ *   colidx_cat[eoff[G]]: graph g's neighbour ids (local, 0 <= id < n_g) at
+ *     colidx_cat[eoff[g] ..]; each graph symmetric with no self loops;
+ *   priority: NULL (index order) or voff[G] uint32 keys (graph g's at
+ *     priority[voff[g] ..]);
+ * Outputs (device): colors_out[voff[G]] (colors >= 1), ncolors_out[G],
+ *   rounds_out[G] (0 for an empty graph).
+ *
+ * gc_batch_create plans the batch: it checks the offsets and every graph's
+ * rowptr, builds the union rowptr, scans degrees, allocates the plan's
+ * workspace (roughly 80 bytes per vertex plus 12 per adjacency entry) and, with
+ * opt->validate, checks ids, self loops and symmetry.  It synchronises
+ * `stream`.  The plan keeps the array pointers: later runs read the caller's
+ * colidx_cat and priority and write the outputs, so their contents may change
+ * between runs, but rowptr_cat is read only here (the degrees are fixed).
+ * opt: as for gc_color_ex; loop_mode must be 0; telemetry is ignored.
+ * Returns GC_OK, GC_ERR_INVALID, GC_ERR_BAD_GRAPH, GC_ERR_OOM or GC_ERR_CUDA;
+ * on failure *plan is NULL.
+ */
+typedef struct gc_batch gc_batch;
+
+int gc_batch_create(const int32_t* rowptr_cat, const int32_t* colidx_cat, const int64_t* vertex_offsets,
+                    const int64_t* edge_offsets, int32_t num_graphs, const uint32_t* priority,
+                    int32_t* colors_out, int32_t* ncolors_out, int32_t* rounds_out, const gc_options* opt,
+                    void* stream, gc_batch** plan);
+
+/* gc_batch_run - enqueue one coloring of the planned batch on `stream`:
+ * memsets and kernels only (no allocation, no host synchronisation), so it
+ * may be captured into a CUDA graph.  Read the status with gc_batch_status. */
+int gc_batch_run(gc_batch* plan, void* stream);
+
+/* gc_batch_launch_graph - the first call captures gc_batch_run into a CUDA
+ * graph (on a private stream) and instantiates it; every call launches that
+ * graph on `stream`. */
+int gc_batch_launch_graph(gc_batch* plan, void* stream);
+
+/* gc_batch_status - wait for `stream`, then report the last run: the largest
+ * round count and color count over the batch, and GC_OK, GC_ERR_BAD_GRAPH (a
+ * neighbour id outside its graph; it was replaced by 0), GC_ERR_MAX_ROUNDS
+ * or GC_ERR_TIMEOUT. */
+int gc_batch_status(gc_batch* plan, void* stream, int32_t* max_rounds, int32_t* max_colors);
+
+/* gc_batch_destroy - free the plan (waits for the device); NULL is a no-op. */
+int gc_batch_destroy(gc_batch* plan);
+
+/* Bytes of device memory the plan holds; kernels one run launches. */
+size_t gc_batch_workspace_bytes(const gc_batch* plan);
+int64_t gc_batch_launch_count(const gc_batch* plan);
+
+/*
+ * Autotuning.  Results never depend on the options (every option set gives
+ * the same colors); only the time does.  These time a list of candidate
+ * option sets on the caller's own input with CUDA events on `stream` (one
+ * warm-up run, then `reps` timed runs each; the median goes to ms_out[c])
+ * and return the index of the fastest in *best.  Candidates that change the
+ * degree-bin limits or the block shape are the intended use.
+ *
+ * gc_tune: one graph, through gc_color_ex (colors_scratch: n int32, device).
+ * gc_batch_tune: one batch, each candidate planned with gc_batch_create and
+ * timed through gc_batch_launch_graph (arguments as for gc_batch_create).
+ * Return GC_OK or the first error of a candidate's run.
+ */
+int gc_tune(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+            int32_t* colors_scratch, const gc_options* candidates, int32_t count, int32_t reps, void* stream,
+            float* ms_out, int32_t* best);
+int gc_batch_tune(const int32_t* rowptr_cat, const int32_t* colidx_cat, const int64_t* vertex_offsets,
+                  const int64_t* edge_offsets, int32_t num_graphs, const uint32_t* priority, int32_t* colors_out,
+                  int32_t* ncolors_out, int32_t* rounds_out, const gc_options* candidates, int32_t count,
+                  int32_t reps, void* stream, float* ms_out, int32_t* best);
+
+/*
  * Learned priority.  The paper colors in index order (Sec. 3.2) and cites
  * vertex-ordering heuristics for Algorithm 1 (smallest-last, largest-first;
  * Sec. 1, Sec. 3.1).  These entry points compute per-vertex features, run a

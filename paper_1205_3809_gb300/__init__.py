@@ -37,7 +37,9 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_last_cuda_error", "gc_release", "gc_workspace_bytes", "gc_last_launch_count",
             "gc_last_round_stats", "gc_last_phase_ms", "gc_color_noalloc", "gc_noalloc_capacity_bytes",
             "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
-            "gc_priority_keys", "gc_mlp_train_step")
+            "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
+            "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
+            "gc_batch_launch_count", "gc_tune", "gc_batch_tune")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -119,6 +121,25 @@ def _load():
         for f in (lib.gc_features, lib.gc_mlp_forward, lib.gc_mlp_grad, lib.gc_mlp_adam,
                   lib.gc_priority_keys, lib.gc_mlp_param_count):
             f.restype = ctypes.c_int
+        lib.gc_batch_create.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, ctypes.POINTER(Options), vp,
+                                        ctypes.POINTER(vp)]
+        lib.gc_batch_run.argtypes = [vp, vp]
+        lib.gc_batch_launch_graph.argtypes = [vp, vp]
+        lib.gc_batch_status.argtypes = [vp, vp, i32p, i32p]
+        lib.gc_batch_destroy.argtypes = [vp]
+        lib.gc_batch_workspace_bytes.argtypes = [vp]
+        lib.gc_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.gc_batch_launch_count.argtypes = [vp]
+        lib.gc_batch_launch_count.restype = ctypes.c_int64
+        for f in (lib.gc_batch_create, lib.gc_batch_run, lib.gc_batch_launch_graph, lib.gc_batch_status,
+                  lib.gc_batch_destroy):
+            f.restype = ctypes.c_int
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.gc_tune.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(Options), i32, i32, vp, fp, i32p]
+        lib.gc_batch_tune.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, ctypes.POINTER(Options), i32, i32, vp,
+                                      fp, i32p]
+        lib.gc_tune.restype = ctypes.c_int
+        lib.gc_batch_tune.restype = ctypes.c_int
         lib.gc_last_phase_ms.argtypes = [vp, i32]
         for f in (lib.gc_color, lib.gc_color_ex, lib.gc_color_host, lib.gc_validate_csr,
                   lib.gc_last_cuda_error, lib.gc_release, lib.gc_last_round_stats,
@@ -446,3 +467,240 @@ def color_learned(rowptr, colidx, params=None, *, options=None, stream=None, rou
         params = load_priority_model(device=rowptr.device)
     keys = learned_priority(rowptr, colidx, params, stream=stream)
     return color(rowptr, colidx, keys, options=options, stream=stream, round_sizes=round_sizes)
+
+
+# ---------------------------------------------------------------- batched coloring
+
+def pack_batch(graphs):
+    """Lay per-graph CSRs end to end in the batched input layout.
+
+    graphs: iterable of (rowptr, colidx) numpy int32 pairs (each graph's own ids).
+    Returns (rowptr_cat, colidx_cat, vertex_offsets, edge_offsets) as numpy arrays.
+    """
+    rps, cis, nv, ne = [], [], [0], [0]
+    for rp, ci in graphs:
+        rp = np.asarray(rp, dtype=np.int32)
+        ci = np.asarray(ci, dtype=np.int32)
+        rps.append(rp)
+        cis.append(ci)
+        nv.append(nv[-1] + rp.shape[0] - 1)
+        ne.append(ne[-1] + ci.shape[0])
+    rowptr_cat = np.concatenate(rps) if rps else np.zeros(0, np.int32)
+    colidx_cat = np.concatenate(cis) if cis else np.zeros(0, np.int32)
+    return rowptr_cat, colidx_cat, np.asarray(nv, np.int64), np.asarray(ne, np.int64)
+
+
+class Batch:
+    """A planned batch of independent graphs colored in one persistent launch
+    (``gc_batch_create`` / ``gc_batch_run`` / ``gc_batch_launch_graph``).
+
+    rowptr_cat, colidx_cat: int32 CUDA tensors in the batched layout (see
+    ``pack_batch``); vertex_offsets, edge_offsets: host int64 arrays (G+1);
+    priority: optional 32-bit CUDA tensor of voff[G] keys.  The plan owns its
+    workspace; ``colors`` (voff[G]), ``ncolors`` and ``rounds`` (G) are CUDA
+    tensors written by every run.
+    """
+
+    def __init__(self, rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, priority=None, *,
+                 options=None, stream=None):
+        import torch
+        lib = _load()
+        self._lib = lib
+        voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+        eoff = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+        G = int(voff.shape[0]) - 1
+        if G < 0 or eoff.shape[0] != G + 1:
+            raise ValueError("vertex_offsets and edge_offsets must both have G+1 entries")
+        N, NNZ = int(voff[-1]), int(eoff[-1])
+        dev = rowptr_cat.device
+        self.device = dev
+        self.num_graphs = G
+        self.colors = torch.empty(N, dtype=torch.int32, device=dev)
+        self.ncolors = torch.empty(G, dtype=torch.int32, device=dev)
+        self.rounds = torch.empty(G, dtype=torch.int32, device=dev)
+        rp = _dev_ptr(rowptr_cat, torch.int32, "rowptr_cat", N + G)
+        ci = _dev_ptr(colidx_cat, torch.int32, "colidx_cat", NNZ)
+        pr = None
+        if priority is not None:
+            if priority.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+                raise ValueError("priority must be a 32-bit integer tensor")
+            pr = _dev_ptr(priority, priority.dtype, "priority", N)
+        self._keep = (rowptr_cat, colidx_cat, priority)  # the plan reads these on every run
+        opt = _options(options)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            rc = lib.gc_batch_create(rp, ci, ctypes.c_void_p(voff.ctypes.data), ctypes.c_void_p(eoff.ctypes.data),
+                                     G, pr, _dev_ptr(self.colors, torch.int32, "colors", N),
+                                     _dev_ptr(self.ncolors, torch.int32, "ncolors", G),
+                                     _dev_ptr(self.rounds, torch.int32, "rounds", G),
+                                     ctypes.byref(opt) if opt is not None else None,
+                                     _stream_handle(stream, dev), ctypes.byref(handle))
+        if rc != GC_OK:
+            raise GcError(rc, "gc_batch_create", lib.gc_last_cuda_error())
+        self._h = handle
+
+    def run(self, *, graph: bool = False, stream=None) -> None:
+        """Enqueue one coloring of the batch (as a CUDA graph replay when graph=True)."""
+        import torch
+        fn = self._lib.gc_batch_launch_graph if graph else self._lib.gc_batch_run
+        with torch.cuda.device(self.device):
+            _check(fn(self._h, _stream_handle(stream, self.device)),
+                   "gc_batch_launch_graph" if graph else "gc_batch_run")
+
+    def status(self, stream=None):
+        """Wait for the last run; returns (max rounds, max colors) over the batch."""
+        import torch
+        r, c = ctypes.c_int32(), ctypes.c_int32()
+        with torch.cuda.device(self.device):
+            _check(self._lib.gc_batch_status(self._h, _stream_handle(stream, self.device), ctypes.byref(r),
+                                             ctypes.byref(c)), "gc_batch_status")
+        return int(r.value), int(c.value)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.gc_batch_workspace_bytes(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.gc_batch_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.gc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- autotuning
+
+TUNE_CANDIDATES = tuple({"small_max_degree": sm, "medium_max_degree": mm, "block_threads": bt}
+                        for sm in (8, 16, 32) for mm in (64, 128, 256) for bt in (128, 256))
+
+
+def _tune_cache_path() -> str:
+    return os.environ.get("GC_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "paper_1205_3809_gb300", "autotune.json")
+
+
+def _degree_signature(deg: np.ndarray) -> list:
+    """Size and shape of a degree sequence: n, sum, max and the share of vertices in
+    each log2 degree bucket (two decimals), so graphs of one family share a key."""
+    deg = np.asarray(deg, dtype=np.int64)
+    if deg.size == 0:
+        return [0, 0, 0]
+    hist = np.bincount(np.floor(np.log2(deg + 1)).astype(np.int64))
+    return [int(deg.size), int(deg.sum()), int(deg.max())] + [round(float(h) / deg.size, 2) for h in hist]
+
+
+def _device_key(device) -> str:
+    import torch
+    p = torch.cuda.get_device_properties(device)
+    return f"{p.name}/{p.multi_processor_count}SM"
+
+
+def _cache_io(key, value=None):
+    import json
+    path = _tune_cache_path()
+    data = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+    if value is None:
+        return data.get(key)
+    data[key] = value
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, path)
+    return value
+
+
+def _options_array(candidates):
+    arr = (Options * len(candidates))()
+    for i, c in enumerate(candidates):
+        for k, v in dict(c).items():
+            setattr(arr[i], k, int(v))
+    return arr
+
+
+def autotune(rowptr, colidx, priority=None, *, candidates=TUNE_CANDIDATES, reps: int = 3,
+             cache: bool = True, stream=None):
+    """Pick the fastest option set for this graph (``gc_tune``); results are cached per
+    device and degree signature.  Returns (options dict, [(options, ms), ...])."""
+    import json
+    import torch
+    lib = _load()
+    n = int(rowptr.numel()) - 1
+    key = json.dumps(["graph", _device_key(rowptr.device), priority is not None,
+                      _degree_signature(np.diff(rowptr.cpu().numpy().astype(np.int64)))])
+    if cache:
+        hit = _cache_io(key)
+        if hit is not None:
+            return hit["best"], [tuple(t) for t in hit["table"]]
+    cands = list(candidates)
+    arr = _options_array(cands)
+    ms = (ctypes.c_float * len(cands))()
+    best = ctypes.c_int32()
+    scratch = torch.empty(max(n, 1), dtype=torch.int32, device=rowptr.device)
+    pr = None if priority is None else _dev_ptr(priority, priority.dtype, "priority", n)
+    with torch.cuda.device(rowptr.device):
+        _check(lib.gc_tune(_dev_ptr(rowptr, torch.int32, "rowptr", None), _dev_ptr(colidx, torch.int32, "colidx", None),
+                           n, pr, ctypes.c_void_p(scratch.data_ptr()), arr, len(cands), int(reps),
+                           _stream_handle(stream, rowptr.device), ms, ctypes.byref(best)), "gc_tune")
+    table = [(dict(c), float(ms[i])) for i, c in enumerate(cands)]
+    result = dict(cands[best.value])
+    if cache:
+        _cache_io(key, {"best": result, "table": table})
+    return result, table
+
+
+def autotune_batch(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, priority=None, *,
+                   candidates=TUNE_CANDIDATES, reps: int = 2, cache: bool = True, stream=None):
+    """Pick the fastest option set for a batch (``gc_batch_tune``); cached per device and
+    the batch's degree signature.  Returns (options dict, [(options, ms), ...])."""
+    import json
+    import torch
+    lib = _load()
+    voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+    eoff = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+    G = int(voff.shape[0]) - 1
+    N = int(voff[-1])
+    rp = rowptr_cat.cpu().numpy().astype(np.int64)
+    keep = np.ones(max(rp.shape[0] - 1, 0), dtype=bool)
+    keep[(voff[1:] + np.arange(G))[:-1]] = False   # the step from one graph's rowptr to the next
+    key = json.dumps(["batch", _device_key(rowptr_cat.device), G, priority is not None,
+                      _degree_signature(np.diff(rp)[keep] if rp.size > 1 else np.zeros(0))])
+    if cache:
+        hit = _cache_io(key)
+        if hit is not None:
+            return hit["best"], [tuple(t) for t in hit["table"]]
+    cands = list(candidates)
+    arr = _options_array(cands)
+    ms = (ctypes.c_float * len(cands))()
+    best = ctypes.c_int32()
+    dev = rowptr_cat.device
+    colors = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+    nc = torch.empty(max(G, 1), dtype=torch.int32, device=dev)
+    rd = torch.empty(max(G, 1), dtype=torch.int32, device=dev)
+    pr = None if priority is None else _dev_ptr(priority, priority.dtype, "priority", N)
+    with torch.cuda.device(dev):
+        _check(lib.gc_batch_tune(_dev_ptr(rowptr_cat, torch.int32, "rowptr_cat", N + G),
+                                 _dev_ptr(colidx_cat, torch.int32, "colidx_cat", int(eoff[-1])),
+                                 ctypes.c_void_p(voff.ctypes.data), ctypes.c_void_p(eoff.ctypes.data), G, pr,
+                                 ctypes.c_void_p(colors.data_ptr()), ctypes.c_void_p(nc.data_ptr()),
+                                 ctypes.c_void_p(rd.data_ptr()), arr, len(cands), int(reps),
+                                 _stream_handle(stream, dev), ms, ctypes.byref(best)), "gc_batch_tune")
+    table = [(dict(c), float(ms[i])) for i, c in enumerate(cands)]
+    result = dict(cands[best.value])
+    if cache:
+        _cache_io(key, {"best": result, "table": table})
+    return result, table

@@ -17,10 +17,12 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <type_traits>
 #include <vector>
 
 #include "gc.h"
+#include "gc_batch.cuh"
 #include "gc_device.cuh"
 
 namespace {
@@ -354,6 +356,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
             p.X0 = (T*)(base + L.x0);
             p.X1 = (T*)(base + L.x1);
             p.colors_out = colors_out;
+            p.settle_round = nullptr;
             p.act0 = (int32_t*)(base + L.act0);
             p.act1 = (int32_t*)(base + L.act1);
             p.stat = (uint32_t*)(base + L.stat);
@@ -538,6 +541,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
             p.X0 = (T*)(base + L.x0);
             p.X1 = (T*)(base + L.x1);
             p.colors_out = colors_out;
+            p.settle_round = nullptr;
             p.act0 = (int32_t*)(base + L.act0);
             p.act1 = (int32_t*)(base + L.act1);
             p.stat = (uint32_t*)(base + L.stat);
@@ -582,6 +586,338 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
         *ncolors = hst.max_color;
         return GC_OK;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched coloring (gc_batch_*): many independent graphs in one persistent
+// launch, as the disjoint union of the graphs (device side: gc_batch.cuh).
+//
+// gc_batch_create does everything that needs the host: it checks the
+// offsets, builds the union rowptr, scans its degrees, picks the color width
+// (16-bit state whenever max degree + 1 < 2^15, so a run can never overflow),
+// sizes and allocates the plan's own workspace, and optionally validates the
+// union graph.  gc_batch_run then only enqueues device work (memsets and
+// kernels; no allocation, no host synchronisation), so a stream capture of
+// it is a CUDA graph of the whole batch, which gc_batch_launch_graph builds
+// once and replays.
+
+template <typename T>
+void fill_workspace(Params<T>& p, char* base, const Layout& L, RoundState* st, int64_t round_cap) {
+    p.X0 = (T*)(base + L.x0);
+    p.X1 = (T*)(base + L.x1);
+    p.act0 = (int32_t*)(base + L.act0);
+    p.act1 = (int32_t*)(base + L.act1);
+    p.stat = (uint32_t*)(base + L.stat);
+    p.SA = (int4*)(base + L.S[0]);
+    p.MA = (int4*)(base + L.M[0]);
+    p.HA = (int4*)(base + L.H[0]);
+    p.HcA = (int32_t*)(base + L.Hc[0]);
+    p.OA = (int32_t*)(base + L.O[0]);
+    p.SB = (int4*)(base + L.S[1]);
+    p.MB = (int4*)(base + L.M[1]);
+    p.HB = (int4*)(base + L.H[1]);
+    p.HcB = (int32_t*)(base + L.Hc[1]);
+    p.OB = (int32_t*)(base + L.O[1]);
+    p.defer = (int32_t*)(base + L.defer);
+    p.hubs = (gc::HubRecord*)(base + L.hubs);
+    p.st = st;
+    p.round_sizes = (int32_t*)(base + L.rs);
+    p.round_vol = (unsigned long long*)(base + L.rv);
+    p.round_cap = (int32_t)round_cap;
+}
+
+}  // namespace
+
+struct gc_batch {
+    int device = -1;
+    int32_t G = 0;
+    int64_t N = 0, NNZ = 0;
+    const int32_t* colidx_cat = nullptr;
+    const uint32_t* prio = nullptr;
+    int32_t* colors_out = nullptr;
+    int32_t* ncolors_out = nullptr;
+    int32_t* rounds_out = nullptr;
+    gc_options o{};
+    int bits = 16;
+    int sms = 0;
+    int per_sm = 0;           // co-resident blocks of the rounds kernel per SM
+    gc::Stats hs{};
+    Layout L{};
+    int64_t round_cap = 1;
+    // plan-owned memory: [head: round state .. of the coloring layout][voff][eoff][rowptr_g][colidx_g][settle][flags]
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t off_voff = 0, off_eoff = 0, off_rowptr = 0, off_colidx = 0, off_settle = 0, off_flags = 0;
+    int64_t launches_per_run = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <typename T>
+int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
+    char* base = (char*)b.ws;
+    const int64_t* voff = (const int64_t*)(base + b.off_voff);
+    const int64_t* eoff = (const int64_t*)(base + b.off_eoff);
+    int32_t* rowptr_g = (int32_t*)(base + b.off_rowptr);
+    int32_t* colidx_g = (int32_t*)(base + b.off_colidx);
+    int32_t* settle = (int32_t*)(base + b.off_settle);
+    gc::BatchFlags* fl = (gc::BatchFlags*)(base + b.off_flags);
+    RoundState* st = (RoundState*)(base + b.L.st);
+    GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
+    GC_CUDA(cudaMemsetAsync(base + b.L.rv, 0, (size_t)b.round_cap * sizeof(unsigned long long), s));
+    GC_CUDA(cudaMemsetAsync(base + b.L.hubs, 0, (size_t)b.hs.cap[gc::kBinH] * sizeof(gc::HubRecord), s));
+    GC_CUDA(cudaMemsetAsync(&fl->bad_colidx, 0, sizeof(int), s));
+    int64_t launches = 0;
+    if (b.NNZ > 0) {
+        const int64_t spans = (b.NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b.sms * 8));
+        gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(b.colidx_cat, voff, eoff, b.G, b.NNZ, colidx_g, fl);
+        GC_CUDA(cudaGetLastError());
+        ++launches;
+    }
+    Params<T> p;
+    p.rowptr = rowptr_g;
+    p.colidx = colidx_g;
+    p.prio = b.prio;
+    p.n = (int32_t)b.N;
+    p.s_max = b.o.small_max_degree;
+    p.m_max = b.o.medium_max_degree;
+    p.max_rounds = b.o.max_rounds > 0 ? b.o.max_rounds : (int32_t)b.N;
+    p.color_limit = b.bits == 16 ? 0x8000u : 0x80000000u;
+    p.colors_out = b.colors_out;
+    p.settle_round = settle;
+    fill_workspace(p, base, b.L, st, b.round_cap);
+    {
+        const int64_t want = (b.N + 255) / 256;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b.sms * 8));
+        gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p);
+        GC_CUDA(cudaGetLastError());
+        gc::pass1_long_kernel<T><<<b.sms * 2, 256, 0, s>>>(p);
+        GC_CUDA(cudaGetLastError());
+        launches += 2;
+    }
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(b.per_sm * b.sms));
+        cfg.blockDim = dim3((unsigned)b.o.block_threads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        GC_CUDA(cudaLaunchKernelEx(&cfg, gc::rounds_persistent_kernel<T>, p));
+        ++launches;
+    }
+    {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)b.G + 7) / 8, (int64_t)b.sms * 8));
+        gc::batch_reduce_kernel<<<grid, 256, 0, s>>>(b.colors_out, settle, voff, b.G, b.ncolors_out,
+                                                     b.rounds_out);
+        GC_CUDA(cudaGetLastError());
+        ++launches;
+    }
+    b.launches_per_run = launches;
+    return GC_OK;
+}
+
+int batch_enqueue(gc_batch& b, cudaStream_t s) {
+    int dev = -1;
+    GC_CUDA(cudaGetDevice(&dev));
+    if (dev != b.device) return GC_ERR_INVALID;
+    if (b.G == 0 || b.N == 0) return GC_OK;
+    return b.bits == 16 ? batch_enqueue_typed<uint16_t>(b, s) : batch_enqueue_typed<int32_t>(b, s);
+}
+
+void batch_free(gc_batch* b) {
+    if (!b) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (b->device >= 0) cudaSetDevice(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(b->ws);
+    }
+    cudaSetDevice(cur);
+    (void)cudaGetLastError();
+    delete b;
+}
+
+int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, const int64_t* voff_h,
+                        const int64_t* eoff_h, int32_t G, const uint32_t* prio, int32_t* colors_out,
+                        int32_t* ncolors_out, int32_t* rounds_out, const gc_options* opt, cudaStream_t s,
+                        gc_batch* b) {
+    int rc = normalise(opt, &b->o);
+    if (rc != GC_OK) return rc;
+    if (b->o.loop_mode != 0) return GC_ERR_INVALID;
+    if (G < 0 || !voff_h || !eoff_h) return GC_ERR_INVALID;
+    if (voff_h[0] != 0 || eoff_h[0] != 0) return GC_ERR_INVALID;
+    for (int32_t g = 0; g < G; ++g)
+        if (voff_h[g + 1] < voff_h[g] || eoff_h[g + 1] < eoff_h[g]) return GC_ERR_INVALID;
+    const int64_t N = voff_h[G], NNZ = eoff_h[G];
+    if (N >= INT32_MAX || NNZ >= INT32_MAX) return GC_ERR_INVALID;
+    if (G > 0 && (!rowptr_cat || !ncolors_out || !rounds_out)) return GC_ERR_INVALID;
+    if (N > 0 && !colors_out) return GC_ERR_INVALID;
+    if (NNZ > 0 && !colidx_cat) return GC_ERR_INVALID;
+    GC_CUDA(cudaGetDevice(&b->device));
+    GC_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
+    int coop = 0;
+    GC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
+    if (!coop) return GC_ERR_CUDA;
+    b->G = G;
+    b->N = N;
+    b->NNZ = NNZ;
+    b->colidx_cat = colidx_cat;
+    b->prio = prio;
+    b->colors_out = colors_out;
+    b->ncolors_out = ncolors_out;
+    b->rounds_out = rounds_out;
+    if (G == 0 || N == 0) {
+        // nothing to color; per-graph results are all zero
+        if (G > 0) {
+            GC_CUDA(cudaMemsetAsync(ncolors_out, 0, (size_t)G * 4, s));
+            GC_CUDA(cudaMemsetAsync(rounds_out, 0, (size_t)G * 4, s));
+            GC_CUDA(cudaStreamSynchronize(s));
+        }
+        return GC_OK;
+    }
+
+    // head: offsets, union rowptr, flags, stats (sized before the degrees are known)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + std::max<size_t>(bytes, 16), 256);
+        return o;
+    };
+    const size_t h_voff = take((size_t)(G + 1) * 8), h_eoff = take((size_t)(G + 1) * 8);
+    const size_t h_rowptr = take((size_t)(N + 1) * 4), h_flags = take(sizeof(gc::BatchFlags));
+    const size_t h_stats = take(sizeof(Stats));
+    const size_t head = off;
+    void* tmp = nullptr;
+    GC_CUDA(cudaMalloc(&tmp, head));
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        return code;
+    };
+    char* hb = (char*)tmp;
+    if (cudaMemcpyAsync(hb + h_voff, voff_h, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(hb + h_eoff, eoff_h, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(hb + h_flags, 0, sizeof(gc::BatchFlags), s) != cudaSuccess ||
+        cudaMemsetAsync(hb + h_stats, 0, sizeof(Stats), s) != cudaSuccess)
+        return fail(GC_ERR_CUDA);
+    {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)b->sms * 8));
+        gc::batch_rowptr_kernel<<<grid, 256, 0, s>>>(rowptr_cat, (const int64_t*)(hb + h_voff),
+                                                     (const int64_t*)(hb + h_eoff), G, N,
+                                                     (int32_t*)(hb + h_rowptr), (gc::BatchFlags*)(hb + h_flags));
+        gc::stats_kernel<<<grid, 256, 0, s>>>((const int32_t*)(hb + h_rowptr), (int32_t)N,
+                                              b->o.small_max_degree, b->o.medium_max_degree,
+                                              (Stats*)(hb + h_stats));
+        if (cudaGetLastError() != cudaSuccess) return fail(GC_ERR_CUDA);
+    }
+    gc::BatchFlags hf;
+    if (cudaMemcpyAsync(&hf, hb + h_flags, sizeof(hf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&b->hs, hb + h_stats, sizeof(Stats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(GC_ERR_CUDA);
+    if (hf.bad_rowptr || b->hs.bad || b->hs.nnz != NNZ) return fail(GC_ERR_BAD_GRAPH);
+    b->bits = b->o.color_bits == 32 || b->hs.max_degree + 1 >= 0x8000 ? 32 : 16;
+
+    // the whole plan: head, then the coloring layout, union colidx and settle rounds
+    const int32_t max_rounds = b->o.max_rounds > 0 ? b->o.max_rounds : (int32_t)N;
+    b->round_cap = std::max<int64_t>(1, std::min<int64_t>(max_rounds, 4096));
+    b->L = make_layout(N, NNZ, b->bits == 16 ? 2 : 4, b->hs, b->round_cap);
+    off = align_up(head, 256);
+    const size_t lay = take(b->L.total);
+    b->off_colidx = take((size_t)NNZ * 4);
+    b->off_settle = take((size_t)N * 4);
+    b->ws_bytes = off;
+    b->off_voff = h_voff;
+    b->off_eoff = h_eoff;
+    b->off_rowptr = h_rowptr;
+    b->off_flags = h_flags;
+    {
+        void* ws = nullptr;
+        const cudaError_t e = cudaMalloc(&ws, b->ws_bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA);
+        }
+        b->ws = ws;
+    }
+    if (cudaMemcpyAsync(b->ws, tmp, head, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return fail(GC_ERR_CUDA);
+    fail(GC_OK);  // frees the head copy after the stream drains
+    // the coloring layout's offsets are relative to its own base
+    Layout& L = b->L;
+    size_t* fields[] = {&L.st, &L.stats, &L.rs, &L.rv, &L.x0, &L.x1, &L.act0, &L.act1, &L.stat, &L.hubs,
+                        &L.defer, &L.S[0], &L.S[1], &L.M[0], &L.M[1], &L.H[0], &L.H[1], &L.Hc[0], &L.Hc[1],
+                        &L.O[0], &L.O[1]};
+    for (size_t* f : fields) *f += lay;
+
+    int per_sm = 0;
+    if (b->bits == 16) {
+        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<uint16_t>,
+                                                              b->o.block_threads, 0));
+    } else {
+        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<int32_t>,
+                                                              b->o.block_threads, 0));
+    }
+    if (per_sm < 1) return GC_ERR_CUDA;
+    b->per_sm = per_sm;
+
+    if (b->o.validate) {
+        char* base = (char*)b->ws;
+        gc::BatchFlags* fl = (gc::BatchFlags*)(base + b->off_flags);
+        const int64_t spans = (NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b->sms * 8));
+        GC_CUDA(cudaMemsetAsync(fl, 0, sizeof(gc::BatchFlags), s));
+        if (NNZ > 0) {
+            gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(colidx_cat, (const int64_t*)(base + b->off_voff),
+                                                         (const int64_t*)(base + b->off_eoff), G, NNZ,
+                                                         (int32_t*)(base + b->off_colidx), fl);
+            GC_CUDA(cudaGetLastError());
+        }
+        GC_CUDA(cudaMemcpyAsync(&hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (hf.bad_colidx) return GC_ERR_BAD_GRAPH;
+        DeviceCache* dcp = nullptr;
+        rc = device_cache(&dcp);
+        if (rc != GC_OK) return rc;
+        int64_t launches = 0;
+        rc = validate_locked((const int32_t*)(base + b->off_rowptr), (const int32_t*)(base + b->off_colidx),
+                             (int32_t)N, s, *dcp, &launches);
+        if (rc != GC_OK) return rc;
+    }
+    GC_CUDA(cudaStreamSynchronize(s));
+    return GC_OK;
+}
+
+int batch_status(gc_batch* b, cudaStream_t s, int32_t* max_rounds, int32_t* max_colors) {
+    if (b->G == 0 || b->N == 0) {
+        if (max_rounds) *max_rounds = 0;
+        if (max_colors) *max_colors = 0;
+        return GC_OK;
+    }
+    char* base = (char*)b->ws;
+    RoundState hst;
+    gc::BatchFlags hf;
+    GC_CUDA(cudaMemcpyAsync(&hst, base + b->L.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaMemcpyAsync(&hf, base + b->off_flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (max_rounds) *max_rounds = hst.rounds;
+    if (max_colors) *max_colors = hst.max_color;
+    if (hf.bad_colidx) return GC_ERR_BAD_GRAPH;
+    if (hst.status == gc::kStatusTimeout) return GC_ERR_TIMEOUT;
+    if (hst.status == gc::kStatusMaxRounds) return GC_ERR_MAX_ROUNDS;
+    if (hst.status != 0) return GC_ERR_CUDA;
+    return GC_OK;
 }
 }  // namespace
 
@@ -736,5 +1072,149 @@ int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n, co
 }
 
 size_t gc_noalloc_capacity_bytes(void) { return kNoAllocBytes; }
+
+int gc_batch_create(const int32_t* rowptr_cat, const int32_t* colidx_cat, const int64_t* vertex_offsets,
+                    const int64_t* edge_offsets, int32_t num_graphs, const uint32_t* priority,
+                    int32_t* colors_out, int32_t* ncolors_out, int32_t* rounds_out, const gc_options* opt,
+                    void* stream, gc_batch** plan) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_last_cuda_error = 0;
+    if (!plan) return GC_ERR_INVALID;
+    *plan = nullptr;
+    gc_batch* b = new (std::nothrow) gc_batch();
+    if (!b) return GC_ERR_OOM;
+    const int rc = batch_create_locked(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, num_graphs, priority,
+                                       colors_out, ncolors_out, rounds_out, opt, (cudaStream_t)stream, b);
+    if (rc != GC_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *plan = b;
+    return GC_OK;
+}
+
+int gc_batch_run(gc_batch* plan, void* stream) {
+    if (!plan) return GC_ERR_INVALID;
+    return batch_enqueue(*plan, (cudaStream_t)stream);
+}
+
+int gc_batch_launch_graph(gc_batch* plan, void* stream) {
+    if (!plan) return GC_ERR_INVALID;
+    gc_batch& b = *plan;
+    int dev = -1;
+    GC_CUDA(cudaGetDevice(&dev));
+    if (dev != b.device) return GC_ERR_INVALID;
+    if (b.G == 0 || b.N == 0) return GC_OK;  // nothing to launch
+    if (!b.exec) {
+        if (!b.cap_stream) GC_CUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
+        GC_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = batch_enqueue(b, b.cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(b.cap_stream, &graph);
+        if (rc != GC_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) g_last_cuda_error = (int)ce;
+            (void)cudaGetLastError();
+            return rc != GC_OK ? rc : GC_ERR_CUDA;
+        }
+        b.graph = graph;
+        GC_CUDA(cudaGraphInstantiate(&b.exec, b.graph, 0));
+    }
+    GC_CUDA(cudaGraphLaunch(b.exec, (cudaStream_t)stream));
+    return GC_OK;
+}
+
+int gc_batch_status(gc_batch* plan, void* stream, int32_t* max_rounds, int32_t* max_colors) {
+    if (!plan) return GC_ERR_INVALID;
+    return batch_status(plan, (cudaStream_t)stream, max_rounds, max_colors);
+}
+
+int gc_batch_destroy(gc_batch* plan) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    batch_free(plan);
+    return GC_OK;
+}
+
+namespace {
+// Median of the timed runs of one candidate.
+float median_ms(std::vector<float>& v) {
+    std::sort(v.begin(), v.end());
+    return v.empty() ? 0.f : v[v.size() / 2];
+}
+}  // namespace
+
+int gc_tune(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+            int32_t* colors_scratch, const gc_options* candidates, int32_t count, int32_t reps, void* stream,
+            float* ms_out, int32_t* best) {
+    if (!candidates || count < 1 || reps < 1 || !ms_out || !best) return GC_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, e = nullptr;
+    GC_CUDA(cudaEventCreate(&a));
+    GC_CUDA(cudaEventCreate(&e));
+    int rc = GC_OK;
+    *best = -1;
+    for (int32_t c = 0; c < count && rc == GC_OK; ++c) {
+        std::vector<float> t;
+        for (int32_t r = 0; r <= reps && rc == GC_OK; ++r) {
+            int32_t nc = 0, rd = 0;
+            std::lock_guard<std::mutex> lock(g_mu);
+            g_last_cuda_error = 0;
+            if (cudaEventRecord(a, s) != cudaSuccess) { rc = GC_ERR_CUDA; break; }
+            rc = color_locked(rowptr, colidx, n, priority, colors_scratch, &nc, &rd, s, &candidates[c], nullptr, 0);
+            if (rc != GC_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e, s) != cudaSuccess || cudaEventSynchronize(e) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, a, e) != cudaSuccess) { rc = GC_ERR_CUDA; break; }
+            if (r > 0) t.push_back(ms);  // the first run of each candidate is a warm-up
+        }
+        if (rc != GC_OK) break;
+        ms_out[c] = median_ms(t);
+        if (*best < 0 || ms_out[c] < ms_out[*best]) *best = c;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(e);
+    return rc;
+}
+
+int gc_batch_tune(const int32_t* rowptr_cat, const int32_t* colidx_cat, const int64_t* vertex_offsets,
+                  const int64_t* edge_offsets, int32_t num_graphs, const uint32_t* priority, int32_t* colors_out,
+                  int32_t* ncolors_out, int32_t* rounds_out, const gc_options* candidates, int32_t count,
+                  int32_t reps, void* stream, float* ms_out, int32_t* best) {
+    if (!candidates || count < 1 || reps < 1 || !ms_out || !best) return GC_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, e = nullptr;
+    GC_CUDA(cudaEventCreate(&a));
+    GC_CUDA(cudaEventCreate(&e));
+    int rc = GC_OK;
+    *best = -1;
+    for (int32_t c = 0; c < count && rc == GC_OK; ++c) {
+        gc_batch* plan = nullptr;
+        rc = gc_batch_create(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, num_graphs, priority, colors_out,
+                             ncolors_out, rounds_out, &candidates[c], stream, &plan);
+        if (rc != GC_OK) break;
+        std::vector<float> t;
+        for (int32_t r = 0; r <= reps && rc == GC_OK; ++r) {
+            float ms = 0.f;
+            if (cudaEventRecord(a, s) != cudaSuccess) { rc = GC_ERR_CUDA; break; }
+            rc = gc_batch_launch_graph(plan, stream);
+            if (rc != GC_OK) break;
+            if (cudaEventRecord(e, s) != cudaSuccess || cudaEventSynchronize(e) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, a, e) != cudaSuccess) { rc = GC_ERR_CUDA; break; }
+            if (r > 0) t.push_back(ms);
+        }
+        if (rc == GC_OK) rc = gc_batch_status(plan, stream, nullptr, nullptr);
+        gc_batch_destroy(plan);
+        if (rc != GC_OK) break;
+        ms_out[c] = median_ms(t);
+        if (*best < 0 || ms_out[c] < ms_out[*best]) *best = c;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(e);
+    return rc;
+}
+
+size_t gc_batch_workspace_bytes(const gc_batch* plan) { return plan ? plan->ws_bytes : 0; }
+
+int64_t gc_batch_launch_count(const gc_batch* plan) { return plan ? plan->launches_per_run : 0; }
 
 }  // extern "C"

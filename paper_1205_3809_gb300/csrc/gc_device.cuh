@@ -137,6 +137,7 @@ struct Params {
     T* X0;
     T* X1;
     int32_t* colors_out;
+    int32_t* settle_round;              // NULL, or receives the round in which each vertex settled
     int32_t* act0;                      // active lists (row starts as in colidx)
     int32_t* act1;
     uint32_t* stat;                     // static masks, 8 words per vertex
@@ -466,6 +467,7 @@ __device__ __forceinline__ void pass1_write(const Params<T>& p, int32_t v, bool 
         p.X0[v] = one;
         p.X1[v] = one;
         p.colors_out[v] = 1;
+        if (p.settle_round) p.settle_round[v] = 1;
         maxc = 1;
     }
 }
@@ -615,6 +617,7 @@ struct PassIO {
     const T* Xc;            // C_k (flagged once settled)
     T* Xcw;                 // the same array, for setting the settled flag
     T* Xn;                  // receives C_{k+1}
+    int k;                  // the round whose Phase 2 this pass runs
     const int32_t* rin;     // active lists read this round (colidx in round 2)
     int32_t* rout;          // active lists written for the next round
     bool first;             // round 2: no static masks yet
@@ -631,6 +634,7 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     io.Xcw = odd ? p.X1 : p.X0;
     io.Xn = odd ? p.X0 : p.X1;
     io.first = k == 2;
+    io.k = k;
     io.rin = k == 2 ? p.colidx : (odd ? p.act1 : p.act0);
     io.rout = odd ? p.act0 : p.act1;
     io.S = odd ? p.SB : p.SA;
@@ -658,6 +662,7 @@ __device__ __forceinline__ void settle(const Params<T>& p, const PassIO<T>& io, 
     io.Xn[v] = word;
     io.Xcw[v] = word;
     p.colors_out[v] = (int32_t)cv;
+    if (p.settle_round) p.settle_round[v] = io.k;
 }
 
 // v takes color c in round k+1.

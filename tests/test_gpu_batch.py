@@ -1,0 +1,210 @@
+"""Batched coloring (many graphs, one persistent launch) against the oracle.
+
+Each graph of a batch must get exactly what the oracle gives it alone: colors,
+color count and round count, bit for bit, whether the batch runs as plain
+launches or as a replayed CUDA graph, with index or key priority.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gcpkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1205_3809_gb300 as m
+    m.library()
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _small_mix():
+    gs = gg.batch_mix(60, 4, n_min=1, n_max=3000)
+    gs.insert(3, gg.edgeless(0))               # an empty graph inside the batch
+    gs.insert(10, gg.complete(40))
+    gs.insert(20, gg.star(700, 350))           # one row above the per-warp threshold
+    gs.insert(30, gg.edgeless(9))
+    gs.append(gg.edgeless(0))                  # and one at the end
+    return gs
+
+
+def _plan(gcpkg, graphs, keys=None, options=None):
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in graphs)
+    pr = None if keys is None else _dev(np.concatenate(keys).view(np.int32))
+    return gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, pr, options=options), voff
+
+
+def _check(graphs, b, voff, keys=None, which=None):
+    colors = b.colors.cpu().numpy()
+    nc = b.ncolors.cpu().numpy()
+    rd = b.rounds.cpu().numpy()
+    for i, g in enumerate(graphs):
+        if which is not None and i not in which:
+            continue
+        ref = oracle.iterative(g.rowptr, g.colidx, None if keys is None else keys[i])
+        got = colors[voff[i]:voff[i + 1]]
+        assert (int(nc[i]), int(rd[i])) == (ref.ncolors, ref.rounds), (i, g.name)
+        assert np.array_equal(got, ref.colors), (i, g.name)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_small_mix_bit_exact(gcpkg, graph):
+    gs = _small_mix()
+    b, voff = _plan(gcpkg, gs)
+    for _ in range(2):                     # a second run (or graph replay) gives the same
+        b.colors.fill_(-1)
+        b.run(graph=graph)
+        mr, mc = b.status()
+        _check(gs, b, voff)
+    assert mr == int(b.rounds.max()) and mc == int(b.ncolors.max())
+    assert b.launch_count >= 4
+    b.close()
+
+
+def test_priority_keys(gcpkg):
+    gs = _small_mix()
+    keys = [(gg.draws(100 + i, 5, g.n) & np.uint64(0xFF)).astype(np.uint32) for i, g in enumerate(gs)]
+    b, voff = _plan(gcpkg, gs, keys)
+    b.run(graph=True)
+    b.status()
+    _check(gs, b, voff, keys)
+
+
+@pytest.mark.parametrize("options", [
+    {"small_max_degree": 8, "medium_max_degree": 64},
+    {"small_max_degree": 1, "medium_max_degree": 1, "block_threads": 128},
+    {"color_bits": 32},
+])
+def test_options_do_not_change_results(gcpkg, options):
+    gs = _small_mix()[:30]
+    b, voff = _plan(gcpkg, gs, options=options)
+    b.run()
+    b.status()
+    _check(gs, b, voff)
+
+
+def test_empty_batches(gcpkg):
+    b = gcpkg.Batch(_dev(np.zeros(0, np.int32)), _dev(np.zeros(0, np.int32)), np.zeros(1, np.int64),
+                    np.zeros(1, np.int64))
+    b.run()
+    assert b.status() == (0, 0)
+    gs = [gg.edgeless(0), gg.edgeless(0)]
+    b, voff = _plan(gcpkg, gs)
+    b.run(graph=True)
+    assert b.status() == (0, 0)
+    assert b.ncolors.cpu().tolist() == [0, 0] and b.rounds.cpu().tolist() == [0, 0]
+
+
+def test_colidx_contents_may_change_between_runs(gcpkg):
+    c = gg.cycle(50)                      # every row has 2 entries: any relabelling keeps rowptr
+    g1 = [c, gg.star(20, 0)]
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in g1)
+    ci_d = _dev(ci)
+    b = gcpkg.Batch(_dev(rp), ci_d, voff, eoff)
+    b.run(graph=True)
+    b.status()
+    _check(g1, b, voff)
+    q = gg.relabel(c, gg.permutation(50, 7))
+    assert np.array_equal(q.rowptr, c.rowptr)
+    ci_d[:c.nnz] = _dev(q.colidx)
+    b.run(graph=True)
+    b.status()
+    _check([q, g1[1]], b, voff)
+    b.close()
+
+
+def test_rejects_bad_inputs(gcpkg):
+    gs = [gg.path(5), gg.cycle(6)]
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+    down = voff.copy()
+    down[1] = voff[2] + 1                              # decreasing offsets, same total
+    with pytest.raises(gcpkg.GcError) as e:
+        gcpkg.Batch(_dev(rp), _dev(ci), down, eoff)
+    assert e.value.code == gcpkg.GC_ERR_INVALID
+    bad = rp.copy()
+    bad[0] = 1                                         # graph 0's rowptr must start at 0
+    with pytest.raises(gcpkg.GcError) as e:
+        gcpkg.Batch(_dev(bad), _dev(ci), voff, eoff)
+    assert e.value.code == gcpkg.GC_ERR_BAD_GRAPH
+    badc = ci.copy()
+    badc[eoff[1]] = 6                                  # id 6 is outside graph 1 (n = 6)
+    with pytest.raises(gcpkg.GcError) as e:
+        gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff, options={"validate": 1})
+    assert e.value.code == gcpkg.GC_ERR_BAD_GRAPH
+    # without validation the run replaces the id, stays in bounds and reports it
+    b = gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff)
+    b.run()
+    with pytest.raises(gcpkg.GcError) as e:
+        b.status()
+    assert e.value.code == gcpkg.GC_ERR_BAD_GRAPH
+    with pytest.raises(gcpkg.GcError) as e:           # loop mode needs the host each round
+        gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options={"loop_mode": 1})
+    assert e.value.code == gcpkg.GC_ERR_INVALID
+
+
+def test_full_size_mix_4096_graphs(gcpkg):
+    """The batched workload: 4,096 graphs, sizes log-uniform in [1,000, 200,000],
+    grids / random geometric / R-MAT-G in turn, seed 4, one CUDA-graph launch.
+    Sampled graphs against the oracle; every graph against gc_color alone on a
+    sample, and every coloring checked for validity."""
+    gs = gg.batch_mix(4096, 4)
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff)
+    b.run(graph=True)
+    b.run(graph=True)
+    b.status()
+    sample = set(range(0, 4096, 173)) | {int(np.argmax([g.n for g in gs]))}
+    _check(gs, b, voff, which=sample)
+    colors = b.colors.cpu().numpy()
+    nc = b.ncolors.cpu().numpy()
+    rd = b.rounds.cpu().numpy()
+    for i in range(0, 4096, 41):
+        g = gs[i]
+        res = gcpkg.color(_dev(g.rowptr), _dev(g.colidx))
+        assert (res.ncolors, res.rounds) == (int(nc[i]), int(rd[i]))
+        assert np.array_equal(res.colors.cpu().numpy(), colors[voff[i]:voff[i + 1]])
+    # validity of every coloring (per graph, to keep host memory small)
+    for i, g in enumerate(gs):
+        c = colors[voff[i]:voff[i + 1]]
+        src = np.repeat(np.arange(g.n, dtype=np.int32), g.degrees)
+        assert np.all(c[src] != c[g.colidx]), i
+        assert g.n == 0 or (c.min() >= 1 and int(nc[i]) == int(c.max()))
+
+
+def test_autotune_graph_and_cache(gcpkg, tmp_path, monkeypatch):
+    monkeypatch.setenv("GC_TUNE_CACHE", str(tmp_path / "tune.json"))
+    g = gg.rmat(14, 8, gg.RMAT_B, 3)
+    rp, ci = _dev(g.rowptr), _dev(g.colidx)
+    cands = [{"small_max_degree": 8, "medium_max_degree": 64, "block_threads": 128},
+             {"small_max_degree": 32, "medium_max_degree": 256, "block_threads": 256}]
+    best, table = gcpkg.autotune(rp, ci, candidates=cands, reps=2)
+    assert best in cands and len(table) == 2 and all(ms > 0 for _, ms in table)
+    again, table2 = gcpkg.autotune(rp, ci, candidates=cands, reps=2)
+    assert again == best and table2 == table          # served from the cache
+    res = gcpkg.color(rp, ci, options=best)
+    ref = oracle.iterative(g.rowptr, g.colidx)
+    assert np.array_equal(res.colors.cpu().numpy(), ref.colors)
+
+
+def test_autotune_batch(gcpkg, tmp_path, monkeypatch):
+    monkeypatch.setenv("GC_TUNE_CACHE", str(tmp_path / "tune.json"))
+    gs = _small_mix()
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+    cands = [{"small_max_degree": 16, "medium_max_degree": 128, "block_threads": 256},
+             {"small_max_degree": 32, "medium_max_degree": 256, "block_threads": 256}]
+    best, table = gcpkg.autotune_batch(_dev(rp), _dev(ci), voff, eoff, candidates=cands, reps=2)
+    assert best in cands and all(ms > 0 for _, ms in table)
+    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options=best)
+    b.run(graph=True)
+    b.status()
+    _check(gs, b, voff)
