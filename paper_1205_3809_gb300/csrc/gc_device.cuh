@@ -63,6 +63,7 @@ constexpr int kPass1Flat = 256;               // pass 1: longer rows take the pe
 #ifndef GC_MED_PER_TASK
 #define GC_MED_PER_TASK 4
 #endif
+
 constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
 constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task (<= 1024 entries)
 constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
@@ -700,9 +701,11 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
 }
 
 // Shared memory of one warp for a flat task.
+// The color windows are stored word-major ([word q][lane]), so the 32 lanes
+// touching word q of their own vertex's window hit 32 different banks.
 struct FlatSmem {
-    uint32_t stat[32 * 8];  // per entry vertex: static mask (+ colors settled this round)
-    uint32_t dyn[32 * 8];   // per entry vertex: colors of unsettled neighbours this round
+    uint32_t stat[8 * 32];  // per entry vertex: static mask (+ colors settled this round)
+    uint32_t dyn[8 * 32];   // per entry vertex: colors of unsettled neighbours this round
     uint32_t conf;          // per entry vertex: conflict flag
     uint32_t lane_of[32];   // lane of the i-th non-empty row
     int32_t vid[32];        // vertex of each lane
@@ -739,16 +742,16 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     if (valid && !io.first) {
         const uint4* src = reinterpret_cast<const uint4*>(p.stat + (size_t)v * 8);
         const uint4 a = __ldcg(src), c = __ldcg(src + 1);
-        sm.stat[lane * 8 + 0] = a.x; sm.stat[lane * 8 + 1] = a.y;
-        sm.stat[lane * 8 + 2] = a.z; sm.stat[lane * 8 + 3] = a.w;
-        sm.stat[lane * 8 + 4] = c.x; sm.stat[lane * 8 + 5] = c.y;
-        sm.stat[lane * 8 + 6] = c.z; sm.stat[lane * 8 + 7] = c.w;
+        sm.stat[0 * 32 + lane] = a.x; sm.stat[1 * 32 + lane] = a.y;
+        sm.stat[2 * 32 + lane] = a.z; sm.stat[3 * 32 + lane] = a.w;
+        sm.stat[4 * 32 + lane] = c.x; sm.stat[5 * 32 + lane] = c.y;
+        sm.stat[6 * 32 + lane] = c.z; sm.stat[7 * 32 + lane] = c.w;
     } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sm.stat[lane * 8 + q] = 0u;
+        for (int q = 0; q < 8; ++q) sm.stat[q * 32 + lane] = 0u;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sm.dyn[lane * 8 + q] = 0u;
+    for (int q = 0; q < 8; ++q) sm.dyn[q * 32 + lane] = 0u;
     if (lane == 0) sm.conf = 0u;
     int32_t incl = len;
 #pragma unroll
@@ -802,9 +805,11 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
                     if (precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u))
                         atomicOr(&sm.conf, 1u << o);
                 }
+            }
+            {
                 const unsigned idx = col - 1u;
-                if (idx < 256u)
-                    atomicOr(settled ? &sm.stat[o * 8 + (idx >> 5)] : &sm.dyn[o * 8 + (idx >> 5)],
+                if (in && idx < 256u)
+                    atomicOr(settled ? &sm.stat[(idx >> 5) * 32 + o] : &sm.dyn[(idx >> 5) * 32 + o],
                              1u << (idx & 31u));
             }
             // survivors: copy to the next round's list, in order within each vertex
@@ -830,7 +835,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
         int ff = -1;
 #pragma unroll
         for (int q = 7; q >= 0; --q) {
-            const uint32_t word = sm.stat[lane * 8 + q] | sm.dyn[lane * 8 + q];
+            const uint32_t word = sm.stat[q * 32 + lane] | sm.dyn[q * 32 + lane];
             if (word != 0xffffffffu) ff = q * 32 + __ffs(~word) - 1;
         }
         if (ff >= 0) color = (uint32_t)ff + 1u;
@@ -848,10 +853,10 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             recolor(p, io, v, color);
             vol += (unsigned)kept;
             uint4* dst = reinterpret_cast<uint4*>(p.stat + (size_t)v * 8);
-            dst[0] = make_uint4(sm.stat[lane * 8 + 0], sm.stat[lane * 8 + 1],
-                                sm.stat[lane * 8 + 2], sm.stat[lane * 8 + 3]);
-            dst[1] = make_uint4(sm.stat[lane * 8 + 4], sm.stat[lane * 8 + 5],
-                                sm.stat[lane * 8 + 6], sm.stat[lane * 8 + 7]);
+            dst[0] = make_uint4(sm.stat[0 * 32 + lane], sm.stat[1 * 32 + lane],
+                                sm.stat[2 * 32 + lane], sm.stat[3 * 32 + lane]);
+            dst[1] = make_uint4(sm.stat[4 * 32 + lane], sm.stat[5 * 32 + lane],
+                                sm.stat[6 * 32 + lane], sm.stat[7 * 32 + lane]);
         } else {
             settle(p, io, v, cv);
             maxc = max(maxc, (int)cv);
@@ -889,6 +894,7 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     __syncwarp();
     HubRecord* rec = p.hubs + h.pos;
     unsigned local = 0;  // survivors written so far (single-chunk vertex)
+    uint32_t rd0 = 0u, rs0 = 0u, rd1 = 0u, rs1 = 0u;  // this lane's colors 1..64 (all, settled)
     for (int32_t sb = lo; sb < hi; sb += kHubSub) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -915,8 +921,17 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
                 if (in) {
                     if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
                     const unsigned idx = col - 1u;
-                    if (idx < 256u) {
-                        const uint32_t bit = 1u << (idx & 31u);
+                    // colors 1..64 gather in registers (one warp reduction per chunk); the
+                    // rest go to the shared windows, where every lane of the warp would
+                    // otherwise hit the same few words
+                    const uint32_t bit = 1u << (idx & 31u);
+                    if (idx < 32u) {
+                        rd0 |= bit;
+                        rs0 |= settled ? bit : 0u;
+                    } else if (idx < 64u) {
+                        rd1 |= bit;
+                        rs1 |= settled ? bit : 0u;
+                    } else if (idx < 256u) {
                         atomicOr(&sm.dyn[idx >> 5], bit);
                         if (settled) atomicOr(&sm.stat[idx >> 5], bit);
                     }
@@ -941,8 +956,13 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     }
     const bool any_conflict = __any_sync(kFull, conflict);
     __syncwarp();
-    const uint32_t word = sm.dyn[lane & 7u];
-    const uint32_t sword = sm.stat[lane & 7u];
+    rd0 = __reduce_or_sync(kFull, rd0);
+    rs0 = __reduce_or_sync(kFull, rs0);
+    rd1 = __reduce_or_sync(kFull, rd1);
+    rs1 = __reduce_or_sync(kFull, rs1);
+    const unsigned q7 = lane & 7u;
+    const uint32_t word = sm.dyn[q7] | (q7 == 0u ? rd0 : (q7 == 1u ? rd1 : 0u));
+    const uint32_t sword = sm.stat[q7] | (q7 == 0u ? rs0 : (q7 == 1u ? rs1 : 0u));
     __syncwarp();
     bool conf;
     int32_t kept;
