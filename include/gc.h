@@ -58,12 +58,15 @@ typedef enum gc_status {
  * Options.  Zero-initialise and set what you need; 0 selects the default.
  */
 typedef struct gc_options {
-    int32_t small_max_degree;  /* vertices of degree <= this are processed by
-                                  4 lanes each, 8 per warp (1..32, default 32) */
-    int32_t medium_max_degree; /* degree <= this (and above the small bin):
-                                  one warp per vertex; above it the adjacency
-                                  is split into 256-entry chunks, one warp
-                                  each (small_max_degree..256, default 256) */
+    int32_t small_max_degree;  /* worklist vertices whose active list has at
+                                  most this many entries go 32 to a warp task
+                                  (1..32, default 32) */
+    int32_t medium_max_degree; /* active lists up to this length (and above
+                                  the small limit) go 4 to a warp task (1 when
+                                  that would leave warps idle); longer lists
+                                  are split into chunks of 1024 entries, one
+                                  warp each (small_max_degree..256, default
+                                  256) */
     int32_t max_rounds;        /* stop with GC_ERR_MAX_ROUNDS after this many
                                   rounds (default n; rounds <= n always holds,
                                   since the first vertex of U in precedence
@@ -83,7 +86,14 @@ typedef struct gc_options {
     int32_t narrow_color_limit; /* testing: with 16-bit state, treat colors >=
                                   this as not fitting (0: 2^15), to exercise
                                   the 32-bit restart */
-    int32_t reserved[7];
+    int32_t tail_volume;       /* persistent launch: once a round reads at
+                                  most this many adjacency entries, one thread
+                                  block runs the remaining rounds alone, with
+                                  block barriers instead of grid barriers
+                                  (0 or negative: never, the default: the
+                                  last rounds are bound by their longest
+                                  task, not by the barrier) */
+    int32_t reserved[6];
 } gc_options;
 
 /*

@@ -82,7 +82,8 @@ class Options(ctypes.Structure):
                 ("max_rounds", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("color_bits", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),
-                ("narrow_color_limit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("narrow_color_limit", ctypes.c_int32), ("tail_volume", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None

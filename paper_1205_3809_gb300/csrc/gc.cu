@@ -223,6 +223,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->small_max_degree == 0) o->small_max_degree = gc::kSmallMaxLimit;
     if (o->medium_max_degree == 0) o->medium_max_degree = gc::kMedMaxLimit;
     if (o->block_threads == 0) o->block_threads = 256;
+    if (o->tail_volume <= 0) o->tail_volume = -1;
     if (o->narrow_color_limit < 0) return GC_ERR_INVALID;
     if (o->small_max_degree < 1 || o->small_max_degree > gc::kSmallMaxLimit) return GC_ERR_INVALID;
     if (o->medium_max_degree < o->small_max_degree || o->medium_max_degree > gc::kMedMaxLimit)
@@ -351,6 +352,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
             p.s_max = o.small_max_degree;
             p.m_max = o.medium_max_degree;
             p.max_rounds = max_rounds;
+            p.tail_volume = o.tail_volume;
             p.color_limit = bits == 16 ? (o.narrow_color_limit > 0 ? (uint32_t)o.narrow_color_limit : 0x8000u)
                                        : 0x80000000u;
             p.X0 = (T*)(base + L.x0);
@@ -537,6 +539,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
             p.s_max = o.small_max_degree;
             p.m_max = o.medium_max_degree;
             p.max_rounds = n;
+            p.tail_volume = o.tail_volume;
             p.color_limit = bits == 16 ? 0x8000u : 0x80000000u;
             p.X0 = (T*)(base + L.x0);
             p.X1 = (T*)(base + L.x1);
@@ -686,6 +689,7 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
     p.s_max = b.o.small_max_degree;
     p.m_max = b.o.medium_max_degree;
     p.max_rounds = b.o.max_rounds > 0 ? b.o.max_rounds : (int32_t)b.N;
+    p.tail_volume = b.o.tail_volume;
     p.color_limit = b.bits == 16 ? 0x8000u : 0x80000000u;
     p.colors_out = b.colors_out;
     p.settle_round = settle;

@@ -108,6 +108,7 @@ struct Stats {
 // down the atomics of blocks still working.
 struct RoundState {
     unsigned cnt[3][4];    // [k % 3] = {|U_k in S|, |U_k in M|, |U_k in H|, chunks of U_k in H}
+    unsigned vol[3];       // [k % 3] = active entries round k reads
     unsigned defer_cnt;    // pass 1: vertices above kPass1Flat
     alignas(128) unsigned bar_count;
     alignas(128) unsigned bar_gen;
@@ -134,6 +135,7 @@ struct Params {
     int32_t n;
     int32_t s_max, m_max;               // length bin limits
     int32_t max_rounds;
+    int32_t tail_volume;                // rounds reading <= this many entries run in block 0 alone (< 0: never)
     uint32_t color_limit;               // a color >= this overflows (16-bit state)
     T* X0;
     T* X1;
@@ -407,11 +409,15 @@ __device__ __forceinline__ void fold_max_color(RoundState* st, int maxc) {
     if (lane_id() == 0 && m > 0) atomicMax(&st->max_color, m);
 }
 
-// Add a warp's share of the next round's read volume to round_vol[r-1].
-__device__ __forceinline__ void fold_volume(unsigned long long* round_vol, int32_t cap, int r,
+// Add a warp's share of round r's read volume to the round counter (vol[r % 3])
+// and to the telemetry (round_vol[r-1]).
+__device__ __forceinline__ void fold_volume(RoundState* st, unsigned long long* round_vol, int32_t cap, int r,
                                             unsigned vol) {
     const unsigned s = __reduce_add_sync(kFull, vol);
-    if (lane_id() == 0 && s && r - 1 < cap) atomicAdd(&round_vol[r - 1], (unsigned long long)s);
+    if (lane_id() == 0 && s) {
+        atomicAdd(&st->vol[r % 3], s);
+        if (r - 1 < cap) atomicAdd(&round_vol[r - 1], (unsigned long long)s);
+    }
 }
 
 // ------------------------------------------------------------ setup scan
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
         warp_append_i32(valid && longrow, v, p.defer, &p.st->defer_cnt);
     }
     fold_max_color(p.st, maxc);
-    fold_volume(p.round_vol, p.round_cap, 2, vol);
+    fold_volume(p.st, p.round_vol, p.round_cap, 2, vol);
 }
 
 // Round 1 for rows longer than kPass1Flat: one warp per vertex, 128
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(256) pass1_long_kernel(Params<T> p) {
         }
     }
     fold_max_color(p.st, maxc);
-    fold_volume(p.round_vol, p.round_cap, 2, vol);
+    fold_volume(p.st, p.round_vol, p.round_cap, 2, vol);
 }
 
 // ------------------------------------------------- fused pass, k >= 2
@@ -682,7 +688,7 @@ struct TaskHead {
 
 template <typename T>
 __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, unsigned nS,
-                                              unsigned nM, unsigned nHC, unsigned tM) {
+                                              unsigned nM, unsigned nHC, unsigned tM, unsigned mpt) {
     TaskHead h;
     h.pos = 0;
     h.lo = 0;
@@ -691,8 +697,8 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
         h.e = __ldcg(io.H + h.pos);
         h.lo = h.e.y + ((int32_t)t - __ldcg(io.Hc + h.pos)) * kChunk;
     } else if (t - nHC < tM) {
-        const unsigned i = (t - nHC) * kMedPerTask + lane_id();
-        h.e = (lane_id() < (unsigned)kMedPerTask && i < nM) ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
+        const unsigned i = (t - nHC) * mpt + lane_id();
+        h.e = (lane_id() < mpt && i < nM) ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
     } else {
         const unsigned i = (t - nHC - tM) * 32 + lane_id();
         h.e = i < nS ? __ldcg(io.S + i) : make_int4(-1, 0, 0, 0);
@@ -1010,28 +1016,29 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     warp_append_one(io.next, make_int4(v, b, kept, h.e.w));
 }
 
-// One fused pass over U_k.  Task t: first the H-bin chunks, then the M-bin
-// entries kMedPerTask at a time, then the S-bin entries 32 at a time (every
-// task reads at most 1024 entries, so no warp holds up the end of a round);
-// warp w takes t = w, w + W, ... and loads the head of its next task before
-// working on the current one.
+// One fused pass over U_k, shared among W warps (this warp is number gw).
+// Task t: first the H-bin chunks, then the M-bin entries kMedPerTask at a
+// time (one at a time when that still leaves warps idle), then the S-bin
+// entries 32 at a time (every task reads at most 1024 entries, so no warp
+// holds up the end of a round); warp gw takes t = gw, gw + W, ... and loads
+// the head of its next task before working on the current one.
 template <typename T>
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
-                                         unsigned nHC, int& maxc) {
+                                         unsigned nHC, int& maxc, unsigned gw, unsigned W) {
     __shared__ FlatSmem s_flat[kWarpsPerBlockMax];
     const PassIO<T> io = pass_io(p, k);
-    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned W = (gridDim.x * blockDim.x) >> 5;
     const unsigned wib = threadIdx.x >> 5;
-    const unsigned tM = (nM + kMedPerTask - 1) / kMedPerTask, tS = (nS + 31) / 32;
+    const unsigned tS = (nS + 31) / 32;
+    const unsigned mpt = nHC + nM + tS <= W ? 1u : (unsigned)kMedPerTask;
+    const unsigned tM = (nM + mpt - 1) / mpt;
     const unsigned total = nHC + tM + tS;
     unsigned vol = 0;  // this lane's share of the next round's read volume
     TaskHead cur;
-    if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM);
+    if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM, mpt);
     for (unsigned t = gw; t < total; t += W) {
         const unsigned tn = t + W;
         TaskHead nxt;
-        if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM);
+        if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
         if (t < nHC) {
             hub_chunk(p, io, cur, s_flat[wib], maxc, vol);
         } else {
@@ -1039,16 +1046,22 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         }
         cur = nxt;
     }
-    fold_volume(p.round_vol, p.round_cap, k + 1, vol);
+    fold_volume(p.st, p.round_vol, p.round_cap, k + 1, vol);
 }
 
 // All rounds k >= 2 in one cooperative launch; a bounded grid barrier
 // separates the rounds.  Every block reads the same counts and status after
-// a barrier, so all blocks leave the loop in the same round.
+// a barrier, so all blocks take the same decisions in the same round.  Once a
+// round reads at most p.tail_volume entries, block 0 runs the remaining rounds
+// alone, separated by block barriers (the other blocks leave): the same
+// synchronous rounds, without the cost of a grid barrier per round.
 template <typename T>
 __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
+    unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned W = (gridDim.x * blockDim.x) >> 5;
+    bool tail = false;
     for (int k = 2;; ++k) {
         const unsigned* c = st->cnt[k % 3];
         const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nH = __ldcg(c + 2),
@@ -1066,13 +1079,24 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
             }
             break;
         }
+        if (!tail && p.tail_volume >= 0 && __ldcg(&st->vol[k % 3]) <= (unsigned)p.tail_volume) {
+            if (blockIdx.x != 0) break;
+            tail = true;
+            gw = threadIdx.x >> 5;
+            W = blockDim.x >> 5;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             unsigned* z = st->cnt[(k + 2) % 3];
             z[0] = z[1] = z[2] = z[3] = 0u;
+            st->vol[(k + 2) % 3] = 0u;
             if (k - 1 < p.round_cap) p.round_sizes[k - 1] = (int32_t)size;
         }
-        run_pass(p, k, nS, nM, nHC, maxc);
-        if (!grid_barrier(st)) break;
+        run_pass(p, k, nS, nM, nHC, maxc, gw, W);
+        if (tail) {
+            __syncthreads();
+        } else if (!grid_barrier(st)) {
+            break;
+        }
     }
     fold_max_color(st, maxc);
 }
@@ -1082,7 +1106,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, kMinBlocks) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
                                                        unsigned nHC) {
     int maxc = 0;
-    run_pass(p, k, nS, nM, nHC, maxc);
+    run_pass(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5);
     fold_max_color(p.st, maxc);
 }
 

@@ -85,6 +85,10 @@ def test_parity_with_priority(gcpkg, make):
     {"block_threads": 128},
     {"narrow_color_limit": 3},                           # restart with 32-bit state
     {"narrow_color_limit": 200, "loop_mode": 1},
+    {"tail_volume": -1},                                 # grid barriers to the end
+    {"tail_volume": 1 << 30},                            # one block runs every round from 2 on
+    {"tail_volume": 3000},                               # the switch happens mid-run
+    {"tail_volume": 1 << 30, "block_threads": 128, "narrow_color_limit": 3},
 ])
 def test_parity_launch_variants(gcpkg, opts):
     for g in [gg.rmat(13, 8, gg.RMAT_B, 7), gg.complete(300), gg.gnm(3000, 30000, 9)]:
@@ -125,10 +129,18 @@ def test_n_zero(gcpkg):
 
 def test_max_rounds_status(gcpkg):
     g = gg.path(50)
-    for mode in (0, 1):
-        res = gcpkg.color(_dev(g.rowptr), _dev(g.colidx), options={"max_rounds": 7, "loop_mode": mode},
-                          check=False)
+    for opts in ({"loop_mode": 0}, {"loop_mode": 1}, {"tail_volume": 1 << 30}, {"tail_volume": -1}):
+        res = gcpkg.color(_dev(g.rowptr), _dev(g.colidx), options={"max_rounds": 7, **opts}, check=False)
         assert res.status == gcpkg.GC_ERR_MAX_ROUNDS and res.rounds == 7
+
+
+def test_tail_switch_round_sizes(gcpkg):
+    """The single-block tail gives the same rounds as grid barriers throughout, on a
+    graph whose last rounds are long (an index-ordered path settles one vertex a round)."""
+    g = gg.from_edges(3000, np.arange(2999), np.arange(1, 3000))
+    for t in (-1, 100, 1 << 30):
+        res = _check(gcpkg, g, options={"tail_volume": t})
+        assert res.rounds == 3000
 
 
 def test_repeat_calls_reuse_workspace(gcpkg):
