@@ -59,6 +59,23 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (each rank times its own replica; the
+    job is as slow as its slowest rank).  One all-reduce on an initialised group."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_rank / max_seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -271,11 +288,8 @@ def run_ours(args):
     clocks = sampler.stop(t0, t1)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = world * args.steps * g.m / total_s
+    total_s = max_over_ranks(total_s, world, dev)
+    value = job_rate(g.m, args.steps, world, total_s)
 
     sizes, vols = gcpkg.last_round_stats()
     elem = 2  # 16-bit color state (the library restarts with 32 bits only past 32767 colors)
@@ -326,7 +340,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "ncolors": res.ncolors, "rounds": res.rounds,
-            "config": {"workload": WORKLOAD if args.scale == SCALE else WORKLOAD.replace("scale 24", f"scale {args.scale}"),
+            "config": {"workload": WORKLOAD if args.scale == SCALE else
+                       WORKLOAD.replace("scale 24", f"scale {args.scale}").replace("16,777,216", f"{g.n:,}"),
                        "n": g.n, "m": g.m, "max_degree": g.max_degree,
                        "priority": "index (plain)", "loop": "persistent cooperative launch",
                        "color_state_bits": 8 * elem,

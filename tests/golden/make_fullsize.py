@@ -23,6 +23,10 @@ WORKLOADS = {
     "rmat_b_s24_seed3": lambda: gg.rmat(24, 8, gg.RMAT_B, 3),
     # R-MAT-G scale 23 (8,388,608 vertices, edge factor 8), (0.45,0.15,0.15,0.25), seed 5
     "rmat_g_s23_seed5": lambda: gg.rmat(23, 8, gg.RMAT_G, 5),
+    # the larger R-MAT-B graphs of Table 4 (scales 25-27), same recipe, seed 3
+    "rmat_b_s25_seed3": lambda: gg.rmat(25, 8, gg.RMAT_B, 3),
+    "rmat_b_s26_seed3": lambda: gg.rmat(26, 8, gg.RMAT_B, 3),
+    "rmat_b_s27_seed3": lambda: gg.rmat(27, 8, gg.RMAT_B, 3),
 }
 
 
