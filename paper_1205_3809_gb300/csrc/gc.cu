@@ -718,8 +718,11 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
         ++launches;
     }
     {
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)b.G + 7) / 8, (int64_t)b.sms * 8));
-        gc::batch_reduce_kernel<<<grid, 256, 0, s>>>(b.colors_out, settle, voff, b.G, b.ncolors_out,
+        GC_CUDA(cudaMemsetAsync(b.ncolors_out, 0, (size_t)b.G * sizeof(int32_t), s));
+        GC_CUDA(cudaMemsetAsync(b.rounds_out, 0, (size_t)b.G * sizeof(int32_t), s));
+        const int64_t chunks = (b.N + gc::kReduceChunk - 1) / gc::kReduceChunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + 7) / 8, (int64_t)b.sms * 8));
+        gc::batch_reduce_kernel<<<grid, 256, 0, s>>>(b.colors_out, settle, voff, b.G, b.N, b.ncolors_out,
                                                      b.rounds_out);
         GC_CUDA(cudaGetLastError());
         ++launches;

@@ -112,25 +112,57 @@ __global__ void __launch_bounds__(256) batch_colidx_kernel(const int32_t* __rest
 }
 
 // Per-graph results: ncolors[g] = max color, rounds[g] = max settle round
-// over graph g's vertices (0 for an empty graph).  One warp per graph.
+// over graph g's vertices (both zeroed beforehand, so an empty graph keeps
+// 0).  The union's vertices are split into equal chunks, one per warp, so a
+// large graph does not serialise on one warp: a chunk inside one graph is
+// reduced by the warp and written with one atomicMax per result; a chunk
+// that crosses graphs lets each lane fold its own run of vertices per graph.
+constexpr int kReduceChunk = 4096;
+
 __global__ void batch_reduce_kernel(const int32_t* __restrict__ colors, const int32_t* __restrict__ settle,
-                                    const int64_t* __restrict__ voff, int32_t G, int32_t* __restrict__ ncolors,
-                                    int32_t* __restrict__ rounds) {
+                                    const int64_t* __restrict__ voff, int32_t G, int64_t N,
+                                    int32_t* __restrict__ ncolors, int32_t* __restrict__ rounds) {
     const unsigned lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = gw; g < G; g += W) {
-        const int64_t b = __ldg(voff + g), e = __ldg(voff + g + 1);
-        int mc = 0, mr = 0;
-        for (int64_t v = b + lane; v < e; v += 32) {
-            mc = max(mc, __ldcg(colors + v));
-            mr = max(mr, __ldcg(settle + v));
-        }
-        mc = __reduce_max_sync(kFull, mc);
-        mr = __reduce_max_sync(kFull, mr);
-        if (lane == 0) {
-            ncolors[g] = mc;
-            rounds[g] = mr;
+    const int64_t chunks = (N + kReduceChunk - 1) / kReduceChunk;
+    for (int64_t ch = gw; ch < chunks; ch += W) {
+        const int64_t v0 = ch * kReduceChunk, v1 = min(N, v0 + kReduceChunk);
+        int32_t g = graph_of(voff, G, v0);
+        int64_t gend = __ldg(voff + g + 1);
+        if (gend >= v1) {
+            int mc = 0, mr = 0;
+            for (int64_t v = v0 + lane; v < v1; v += 32) {
+                mc = max(mc, __ldcg(colors + v));
+                mr = max(mr, __ldcg(settle + v));
+            }
+            mc = __reduce_max_sync(kFull, mc);
+            mr = __reduce_max_sync(kFull, mr);
+            if (lane == 0) {
+                atomicMax(ncolors + g, mc);
+                atomicMax(rounds + g, mr);
+            }
+        } else {
+            int mc = 0, mr = 0;
+            for (int64_t v = v0 + lane; v < v1; v += 32) {
+                if (v >= gend) {
+                    if (mc | mr) {
+                        atomicMax(ncolors + g, mc);
+                        atomicMax(rounds + g, mr);
+                    }
+                    mc = mr = 0;
+                    while (v >= gend) {
+                        ++g;
+                        gend = __ldg(voff + g + 1);
+                    }
+                }
+                mc = max(mc, __ldcg(colors + v));
+                mr = max(mr, __ldcg(settle + v));
+            }
+            if (mc | mr) {
+                atomicMax(ncolors + g, mc);
+                atomicMax(rounds + g, mr);
+            }
         }
     }
 }
