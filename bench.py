@@ -302,6 +302,7 @@ def run_ours(args):
     gather_rate = gathers / (kms / 1e3) / 1e9
 
     learned = None if args.no_learned else measure_learned(gcpkg, rp, ci, g, flush, stream, args)
+    asynchronous = None if args.no_learned else measure_async(gcpkg, rp, ci, g, flush, stream, args)
 
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
@@ -357,6 +358,7 @@ def run_ours(args):
                                         "frac": gather_rate / L2_GATHER_CEILING}},
             "cpu_baseline": cpu,
             "learned": learned,
+            "asynchronous": asynchronous,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -415,6 +417,32 @@ def measure_learned(gcpkg, rp, ci, g, flush, stream, args):
                          "coloring": phase[3]},
             "model": os.path.basename(gcpkg.PRIORITY_MODEL) + " (trained on R-MAT-G scales 14-18)",
             "gpu_launches": launches}
+
+
+def measure_async(gcpkg, rp, ci, g, flush, stream, args):
+    """The asynchronous form of Algorithm 2 on the same graph (Phase 1 reads live
+    colors; schedule-dependent, valid by construction), for colors and rounds beside
+    the synchronous form."""
+    import torch
+    out = torch.empty(g.n, dtype=torch.int32, device=rp.device)
+    for _ in range(2):
+        flush.zero_()
+        res = gcpkg.color_async(rp, ci, out=out, stream=stream)
+    torch.cuda.synchronize()
+    ms, cols, rds = [], [], []
+    for _ in range(max(3, args.steps // 5)):
+        flush.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = gcpkg.color_async(rp, ci, out=out, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+        cols.append(res.ncolors)
+        rds.append(res.rounds)
+    return {"value": g.m / (statistics.mean(ms) / 1e3), "unit": "edges/s", "ms_per_step": statistics.mean(ms),
+            "steps": len(ms), "ncolors": cols, "rounds": rds,
+            "note": "Phase 1 reads live colors (the paper's shared-memory form); colors vary run to run"}
 
 
 def run_batched(args):

@@ -211,6 +211,20 @@ int gc_color_noalloc(const int32_t* rowptr, const int32_t* colidx, int32_t n,
 size_t gc_noalloc_capacity_bytes(void);
 
 /*
+ * gc_color_async - Algorithm 2 (Sec. 3.2) as the paper runs it on shared
+ * memory: Phase 1 reads the one shared color array while other threads
+ * write it (each vertex sees some of this round's tentative colors), Phase 2
+ * sends the later (by priority, then index) of two equally colored
+ * neighbours back.  The colors depend on the schedule: the result is a
+ * proper coloring with every color <= degree + 1, not a fixed one.  Same
+ * arguments as gc_color plus max_rounds (<= 0: n) and stream; device arrays;
+ * synchronises `stream` once per round.  Returns GC_OK, GC_ERR_INVALID,
+ * GC_ERR_OOM, GC_ERR_CUDA or GC_ERR_MAX_ROUNDS.
+ */
+int gc_color_async(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
+                   int32_t* colors_out, int32_t* ncolors, int32_t* rounds, int32_t max_rounds, void* stream);
+
+/*
  * Batched coloring: many independent graphs in one persistent launch.
  *
  * Algorithm 2 (Sec. 3.2) in synchronous rounds on each graph of a batch, all

@@ -39,7 +39,7 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
-            "gc_batch_launch_count", "gc_tune", "gc_batch_tune")
+            "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -67,8 +67,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             and all(os.path.getmtime(LIB_PATH) >= os.path.getmtime(s) for s in srcs)):
         return LIB_PATH
     cmd = ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "-I", _INCLUDE, "--threads", "2", "-o", LIB_PATH + ".tmp",
-           os.path.join(_CSRC, "gc.cu"), os.path.join(_CSRC, "gc_mlp.cu")]
+           "-Xcompiler", "-fPIC", "-shared", "-I", _INCLUDE, "--threads", "3", "-o", LIB_PATH + ".tmp",
+           os.path.join(_CSRC, "gc.cu"), os.path.join(_CSRC, "gc_mlp.cu"), os.path.join(_CSRC, "gc_async.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)
@@ -140,6 +140,8 @@ def _load():
         lib.gc_batch_tune.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, ctypes.POINTER(Options), i32, i32, vp,
                                       fp, i32p]
         lib.gc_tune.restype = ctypes.c_int
+        lib.gc_color_async.argtypes = [vp, vp, i32, vp, vp, i32p, i32p, i32, vp]
+        lib.gc_color_async.restype = ctypes.c_int
         lib.gc_batch_tune.restype = ctypes.c_int
         lib.gc_last_phase_ms.argtypes = [vp, i32]
         for f in (lib.gc_color, lib.gc_color_ex, lib.gc_color_host, lib.gc_validate_csr,
@@ -241,6 +243,28 @@ def color(rowptr, colidx, priority=None, *, out=None, options=None, stream=None,
         res.round_sizes = rs_buf[:min(res.rounds, cap)].copy()
     res.status = rc
     return res
+
+
+def color_async(rowptr, colidx, priority=None, *, out=None, max_rounds: int = 0, stream=None,
+                check: bool = True) -> Result:
+    """Asynchronous Algorithm 2 (``gc_color_async``): schedule-dependent colors, valid
+    by construction; the comparison point for the synchronous ``color``."""
+    import torch
+    lib = _load()
+    n = int(rowptr.numel()) - 1
+    rp = _dev_ptr(rowptr, torch.int32, "rowptr", None)
+    ci = _dev_ptr(colidx, torch.int32, "colidx", None)
+    pr = None if priority is None else _dev_ptr(priority, priority.dtype, "priority", n)
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=rowptr.device)
+    co = _dev_ptr(out, torch.int32, "out", max(n, 0))
+    nc, rd = ctypes.c_int32(), ctypes.c_int32()
+    with torch.cuda.device(rowptr.device):
+        rc = lib.gc_color_async(rp, ci, n, pr, co, ctypes.byref(nc), ctypes.byref(rd), int(max_rounds),
+                                _stream_handle(stream, rowptr.device))
+    if rc != GC_OK and check:
+        raise GcError(rc, "gc_color_async", lib.gc_last_cuda_error())
+    return Result(colors=out, ncolors=int(nc.value), rounds=int(rd.value), status=rc)
 
 
 def color_host(rowptr: np.ndarray, colidx: np.ndarray, priority=None, *, out=None,
