@@ -75,7 +75,10 @@ typedef struct gc_options {
                                   symmetry on the device before coloring */
     int32_t loop_mode;         /* 0: all rounds in one persistent cooperative
                                   launch (default); 1: one launch per round,
-                                  the host reads |U| after each */
+                                  the host reads |U| after each; 2: a CUDA
+                                  graph whose while node runs one round
+                                  kernel per round and decides on the device
+                                  whether to go on */
     int32_t color_bits;        /* 0 or 16: 16-bit color state (a flag bit and
                                   colors below 2^15), and if a color does not
                                   fit, the call starts over with 32-bit state;

@@ -148,6 +148,71 @@ Layout make_layout(int64_t n, int64_t nnz, size_t elem, const Stats& hs, int64_t
     return L;
 }
 
+// Loop mode 2: rounds 2.. as one CUDA graph: a condition kernel, then a while
+// node whose body is one round kernel and the condition kernel, so the loop
+// runs on the device without a cooperative launch or host round trips.  The
+// graph is built for this call's parameters and freed after it has run.
+template <typename T>
+int run_rounds_graph(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
+    int per_sm = 0;
+    GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::graph_round_kernel<T>, o.block_threads, 0));
+    if (per_sm < 1) return GC_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GC_CUDA(cudaGraphCreate(&g, 0));
+    int rc = GC_OK;
+    auto check = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == GC_OK) {
+            g_last_cuda_error = (int)e;
+            (void)cudaGetLastError();
+            rc = e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA;
+        }
+        return e == cudaSuccess;
+    };
+    cudaGraphConditionalHandle handle;
+    int before = 1, inside = 0;
+    if (check(cudaGraphConditionalHandleCreate(&handle, g, 0, 0))) {
+        cudaGraphNodeParams pre = {};
+        pre.type = cudaGraphNodeTypeKernel;
+        void* pre_args[] = {&p, &before, &handle};
+        pre.kernel.func = (void*)gc::graph_cond_kernel<T>;
+        pre.kernel.gridDim = dim3(1);
+        pre.kernel.blockDim = dim3(1);
+        pre.kernel.kernelParams = pre_args;
+        cudaGraphNode_t n_pre = nullptr, n_while = nullptr;
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = handle;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        if (check(cudaGraphAddNode(&n_pre, g, nullptr, nullptr, 0, &pre)) &&
+            check(cudaGraphAddNode(&n_while, g, &n_pre, nullptr, 1, &wp))) {
+            cudaGraph_t body = wp.conditional.phGraph_out[0];
+            cudaGraphNodeParams rk = {};
+            rk.type = cudaGraphNodeTypeKernel;
+            void* rk_args[] = {&p};
+            rk.kernel.func = (void*)gc::graph_round_kernel<T>;
+            rk.kernel.gridDim = dim3((unsigned)(per_sm * dc.sms));
+            rk.kernel.blockDim = dim3((unsigned)o.block_threads);
+            rk.kernel.kernelParams = rk_args;
+            cudaGraphNodeParams ck = pre;
+            void* ck_args[] = {&p, &inside, &handle};
+            ck.kernel.kernelParams = ck_args;
+            cudaGraphNode_t n_round = nullptr, n_cond = nullptr;
+            if (check(cudaGraphAddNode(&n_round, body, nullptr, nullptr, 0, &rk)) &&
+                check(cudaGraphAddNode(&n_cond, body, &n_round, nullptr, 1, &ck)) &&
+                check(cudaGraphInstantiate(&exec, g, 0)) && check(cudaGraphLaunch(exec, s)))
+                *launches += 1;
+        }
+    }
+    if (exec) {
+        check(cudaStreamSynchronize(s));
+        cudaGraphExecDestroy(exec);
+    }
+    cudaGraphDestroy(g);
+    return rc;
+}
+
 template <typename T>
 int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
     const int threads = o.block_threads;
@@ -162,6 +227,7 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
         *launches += 2;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
     }
+    if (o.loop_mode == 2) return run_rounds_graph(o, dc, p, s, launches);
     if (o.loop_mode == 0) {
         int per_sm = 0;
         GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -229,7 +295,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->medium_max_degree < o->small_max_degree || o->medium_max_degree > gc::kMedMaxLimit)
         return GC_ERR_INVALID;
     if (o->block_threads != 128 && o->block_threads != 256) return GC_ERR_INVALID;
-    if (o->loop_mode != 0 && o->loop_mode != 1) return GC_ERR_INVALID;
+    if (o->loop_mode < 0 || o->loop_mode > 2) return GC_ERR_INVALID;
     if (o->color_bits != 0 && o->color_bits != 16 && o->color_bits != 32) return GC_ERR_INVALID;
     if (o->max_rounds < 0 || o->validate < 0 || o->validate > 1) return GC_ERR_INVALID;
     if (o->telemetry != 0 && o->telemetry != 1) return GC_ERR_INVALID;

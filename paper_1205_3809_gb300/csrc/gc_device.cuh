@@ -115,6 +115,7 @@ struct RoundState {
     alignas(128) int status;
     int rounds;
     int max_color;
+    int graph_round;       // loop mode 2: the round the graph's next iteration runs
 };
 
 // Per H-bin vertex of the current round (indexed by its worklist position).
@@ -1121,6 +1122,50 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
     k *= 0xc4ceb9fe1a85ec53ull;
     k ^= k >> 33;
     return k;
+}
+
+// Loop mode 2: the rounds as a CUDA graph whose while node repeats
+// graph_round_kernel + graph_cond_kernel on the device.  graph_round_kernel
+// runs round st->graph_round over the counts that the previous pass left.
+template <typename T>
+__global__ void __launch_bounds__(256, kMinBlocks) graph_round_kernel(Params<T> p) {
+    RoundState* st = p.st;
+    const int k = __ldcg(&st->graph_round);
+    const unsigned* c = st->cnt[k % 3];
+    const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nHC = __ldcg(c + 3);
+    int maxc = 0;
+    run_pass(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5);
+    fold_max_color(st, maxc);
+}
+
+// One thread, after round k (k = 1 before the loop): decide whether round k + 1
+// runs, clear the counters it will append to, and set the while condition.
+template <typename T>
+__global__ void graph_cond_kernel(Params<T> p, int before_loop, cudaGraphConditionalHandle handle) {
+    RoundState* st = p.st;
+    const int k = before_loop ? 1 : st->graph_round;
+    const int kn = k + 1;
+    const unsigned* c = st->cnt[kn % 3];
+    const unsigned size = c[0] + c[1] + c[2];
+    unsigned go = 0u;
+    if (size == 0u) {
+        st->rounds = k;
+    } else if (st->status == kStatusColorOverflow) {
+        st->rounds = k;
+    } else if (kn > p.max_rounds) {
+        st->rounds = k;
+        st->status = kStatusMaxRounds;
+    } else {
+        unsigned* z = st->cnt[(kn + 1) % 3];
+        z[0] = z[1] = z[2] = z[3] = 0u;
+        st->vol[(kn + 1) % 3] = 0u;
+        if (kn - 1 < p.round_cap) p.round_sizes[kn - 1] = (int32_t)size;
+        st->graph_round = kn;
+        go = 1u;
+    }
+    __threadfence();
+    cudaGraphSetConditional(handle, go);
 }
 
 struct ValidateOut {

@@ -85,6 +85,9 @@ def test_parity_with_priority(gcpkg, make):
     {"block_threads": 128},
     {"narrow_color_limit": 3},                           # restart with 32-bit state
     {"narrow_color_limit": 200, "loop_mode": 1},
+    {"loop_mode": 2},                                    # CUDA graph with a device-side while loop
+    {"loop_mode": 2, "color_bits": 32, "block_threads": 128},
+    {"loop_mode": 2, "narrow_color_limit": 3},           # overflow stops the graph, 32-bit restart
     {"tail_volume": -1},                                 # grid barriers to the end
     {"tail_volume": 1 << 30},                            # one block runs every round from 2 on
     {"tail_volume": 3000},                               # the switch happens mid-run
@@ -129,7 +132,8 @@ def test_n_zero(gcpkg):
 
 def test_max_rounds_status(gcpkg):
     g = gg.path(50)
-    for opts in ({"loop_mode": 0}, {"loop_mode": 1}, {"tail_volume": 1 << 30}, {"tail_volume": -1}):
+    for opts in ({"loop_mode": 0}, {"loop_mode": 1}, {"loop_mode": 2}, {"tail_volume": 1 << 30},
+                 {"tail_volume": -1}):
         res = gcpkg.color(_dev(g.rowptr), _dev(g.colidx), options={"max_rounds": 7, **opts}, check=False)
         assert res.status == gcpkg.GC_ERR_MAX_ROUNDS and res.rounds == 7
 
