@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -52,6 +53,19 @@ REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def cpu_model() -> str:
+    """The host CPU's model string, as far as the OS reports it."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
 
 
 def dist_env():
@@ -330,9 +344,17 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cg, cr, ct = oracle_rate(CPU_BASELINE_SCALE)
+        import oracle
+        t = time.perf_counter()
+        _, greedy_colors = oracle.greedy(cg.rowptr, cg.colidx)
+        greedy_s = time.perf_counter() - t
         cpu = {"value": cg.m / ct[0], "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": (f"R-MAT-B scale {CPU_BASELINE_SCALE} (same recipe, seed 3): {cg.m} edges, "
-                          f"one full run, {ct[0]:.1f} s, {cr.rounds} rounds, {cr.ncolors} colors")}
+                          f"one full run, {ct[0]:.1f} s, {cr.rounds} rounds, {cr.ncolors} colors"),
+               "host": {"cpus": os.cpu_count(), "machine": platform.machine(), "model": cpu_model()},
+               "greedy_serial": {"value": cg.m / greedy_s, "unit": "edges/s", "seconds": round(greedy_s, 3),
+                                 "ncolors": greedy_colors,
+                                 "note": "Algorithm 1 in index order, one core (the sequential baseline)"}}
 
     if rank == 0:
         line = {
