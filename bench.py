@@ -551,14 +551,16 @@ def run_batched(args):
 
 
 def measure_l2_ceiling():
+    import shutil
+    import tempfile
     src = os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "l2_gather_probe.cu")
-    exe = os.path.join(ROOT, "gpurun_out", "l2_gather_probe")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    tmp = tempfile.mkdtemp(prefix="gc_probe_")
+    exe = os.path.join(tmp, "l2_gather_probe")
     try:
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
         subprocess.run([exe], check=True)
     finally:
-        os.remove(exe)
+        shutil.rmtree(tmp, ignore_errors=True)
 
 
 def main():

@@ -63,7 +63,7 @@ def main():
     ap.add_argument("--init-seed", type=int, default=1)
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--no-eval", action="store_true")
-    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out", "priority_mlp_rmat_g.json"))
+    ap.add_argument("--out", default=os.path.join(ROOT, "paper_1205_3809_gb300", "priority_mlp_rmat_g.json"))
     a = ap.parse_args()
 
     gg.build()
