@@ -152,10 +152,10 @@ Layout make_layout(int64_t n, int64_t nnz, size_t elem, const Stats& hs, int64_t
 // node whose body is one round kernel and the condition kernel, so the loop
 // runs on the device without a cooperative launch or host round trips.  The
 // graph is built for this call's parameters and freed after it has run.
-template <typename T>
+template <typename T, bool P>
 int run_rounds_graph(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
     int per_sm = 0;
-    GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::graph_round_kernel<T>, o.block_threads, 0));
+    GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::graph_round_kernel<T, P>, o.block_threads, 0));
     if (per_sm < 1) return GC_ERR_CUDA;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -191,7 +191,7 @@ int run_rounds_graph(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStr
             cudaGraphNodeParams rk = {};
             rk.type = cudaGraphNodeTypeKernel;
             void* rk_args[] = {&p};
-            rk.kernel.func = (void*)gc::graph_round_kernel<T>;
+            rk.kernel.func = (void*)gc::graph_round_kernel<T, P>;
             rk.kernel.gridDim = dim3((unsigned)(per_sm * dc.sms));
             rk.kernel.blockDim = dim3((unsigned)o.block_threads);
             rk.kernel.kernelParams = rk_args;
@@ -213,8 +213,8 @@ int run_rounds_graph(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStr
     return rc;
 }
 
-template <typename T>
-int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
+template <typename T, bool P>
+int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
     const int threads = o.block_threads;
     {
         // one warp task per 32 vertices
@@ -227,15 +227,15 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
         *launches += 2;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
     }
-    if (o.loop_mode == 2) return run_rounds_graph(o, dc, p, s, launches);
+    if (o.loop_mode == 2) return run_rounds_graph<T, P>(o, dc, p, s, launches);
     if (o.loop_mode == 0) {
         int per_sm = 0;
         GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, gc::rounds_persistent_kernel<T>, threads, 0));
+            &per_sm, gc::rounds_persistent_kernel<T, P>, threads, 0));
         if (per_sm < 1 || !dc.coop) return GC_ERR_CUDA;
         dim3 grid(per_sm * dc.sms), block(threads);
         void* args[] = {&p};
-        GC_CUDA(cudaLaunchCooperativeKernel((const void*)gc::rounds_persistent_kernel<T>, grid, block,
+        GC_CUDA(cudaLaunchCooperativeKernel((const void*)gc::rounds_persistent_kernel<T, P>, grid, block,
                                             args, 0, s));
         *launches += 1;
         return GC_OK;
@@ -273,7 +273,7 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
         const int64_t warps_per_block = threads / 32;
         const int grid = (int)std::max<int64_t>(
             1, std::min<int64_t>((tasks + warps_per_block - 1) / warps_per_block, (int64_t)dc.sms * 8));
-        gc::round_kernel<T><<<grid, threads, 0, s>>>(p, k, nS, nM, nHC);
+        gc::round_kernel<T, P><<<grid, threads, 0, s>>>(p, k, nS, nM, nHC);
         GC_CUDA(cudaGetLastError());
         *launches += 1;
     }
@@ -281,6 +281,13 @@ int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t 
     GC_CUDA(cudaMemcpyAsync(&st->rounds, &hs[2], sizeof(int), cudaMemcpyHostToDevice, s));
     GC_CUDA(cudaStreamSynchronize(s));
     return GC_OK;
+}
+
+// The round kernels are compiled twice: with a priority array (its order
+// kept as a bit in the active lists) and without (index order).
+template <typename T>
+int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
+    return p.prio ? run_rounds_p<T, true>(o, dc, p, s, launches) : run_rounds_p<T, false>(o, dc, p, s, launches);
 }
 
 int normalise(const gc_options* opt, gc_options* o) {
@@ -780,7 +787,11 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        GC_CUDA(cudaLaunchKernelEx(&cfg, gc::rounds_persistent_kernel<T>, p));
+        if (b.prio) {
+            GC_CUDA(cudaLaunchKernelEx(&cfg, gc::rounds_persistent_kernel<T, true>, p));
+        } else {
+            GC_CUDA(cudaLaunchKernelEx(&cfg, gc::rounds_persistent_kernel<T, false>, p));
+        }
         ++launches;
     }
     {
@@ -936,10 +947,10 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
 
     int per_sm = 0;
     if (b->bits == 16) {
-        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<uint16_t>,
+        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<uint16_t, true>,
                                                               b->o.block_threads, 0));
     } else {
-        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<int32_t>,
+        GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gc::rounds_persistent_kernel<int32_t, true>,
                                                               b->o.block_threads, 0));
     }
     if (per_sm < 1) return GC_ERR_CUDA;

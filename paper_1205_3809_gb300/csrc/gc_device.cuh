@@ -223,6 +223,15 @@ __device__ __forceinline__ int32_t ld_color(const int32_t* a, uint64_t pol) {
     return r;
 }
 
+// With a priority array, active lists written from round 2 on carry, in bit
+// 31 of each entry (ids are below 2^31), whether that neighbour precedes the
+// list's vertex.  The order never changes, so it is computed once (round 2)
+// and later rounds test a bit instead of gathering two priority keys per
+// equally colored neighbour.  Under index priority the test is one compare
+// and the lists carry plain ids.
+constexpr uint32_t kPrecBit = 0x80000000u;
+__device__ __forceinline__ int32_t entry_id(int32_t x) { return x & 0x7fffffff; }
+
 // w precedes v: (prio[w], w) < (prio[v], v); pv = prio[v] (ignored if no prio).
 __device__ __forceinline__ bool precedes(const uint32_t* __restrict__ prio, int32_t w, int32_t v,
                                          uint32_t pv) {
@@ -736,7 +745,7 @@ __device__ __forceinline__ void st_stream(int32_t* a, int32_t x, uint64_t pol) {
 // neighbour has not settled, is copied to the next round's list at the
 // vertex's running write position.  Afterwards each lane decides its own
 // vertex.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en, int bin,
                                           FlatSmem& sm, int& maxc, unsigned& vol) {
     const unsigned lane = lane_id();
@@ -794,7 +803,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
 #pragma unroll
         for (int u = 0; u < kFlatBatches; ++u) {
             const int32_t f = F0 + 32 * u + (int32_t)lane;
-            c[u] = f < D ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+            c[u] = f < D ? ld_color(io.Xc + (P ? entry_id(w[u]) : w[u]), io.pol_col) : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < kFlatBatches; ++u) {
@@ -806,13 +815,22 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             const bool in = f < D;
             const uint32_t col = word_color(c[u]);
             const bool settled = in && word_settled(c[u]);
-            if (in) {
-                if (col == ocv) {
+            // does this neighbour precede its owner?  Round 2 works it out (for the
+            // conflict test and for the bit of every entry it keeps); later rounds read
+            // the bit.
+            const int32_t wid = P ? entry_id(w[u]) : w[u];
+            bool pre = false;
+            if constexpr (!P) {
+                if (in && col == ocv) pre = wid < sm.vid[o];
+            } else if (in && (col == ocv || (io.first && !settled))) {
+                if (io.first) {
                     const int32_t ov = sm.vid[o];
-                    if (precedes(p.prio, w[u], ov, p.prio ? __ldg(p.prio + ov) : 0u))
-                        atomicOr(&sm.conf, 1u << o);
+                    pre = precedes(p.prio, wid, ov, __ldg(p.prio + ov));
+                } else {
+                    pre = w[u] < 0;
                 }
             }
+            if (in && col == ocv && pre) atomicOr(&sm.conf, 1u << o);
             {
                 const unsigned idx = col - 1u;
                 if (in && idx < 256u)
@@ -824,7 +842,10 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             const unsigned kb = __ballot_sync(kFull, keep);
             const int32_t seglo = max(0, oo[u] - base);  // first lane of my vertex in this batch
             const unsigned below = kb & ((1u << lane) - 1u) & ~((1u << seglo) - 1u);
-            if (keep) st_stream(io.rout + ob[u] + okept + __popc(below), w[u], io.pol_row);
+            if (keep)
+                st_stream(io.rout + ob[u] + okept + __popc(below),
+                          (P && io.first) ? (int32_t)((uint32_t)wid | (pre ? kPrecBit : 0u)) : w[u],
+                          io.pol_row);
             // my vertex's lanes in this batch: [lo, hi)
             const int32_t lo = max(0, min(32, off - base));
             const int32_t hi = max(0, min(32, off + len - base));
@@ -883,7 +904,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
 // vertex whose active list fits one chunk is decided by this warp at once;
 // otherwise the chunks OR their results into the vertex's record, and the
 // warp that completes the last chunk decides it and clears the record.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& io, TaskHead h,
                                           FlatSmem& sm, int& maxc, unsigned& vol) {
     constexpr int kHalf = kPerLane / 2;
@@ -916,7 +937,7 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 #pragma unroll
             for (int u = 0; u < kHalf; ++u) {
                 const int32_t j = sb + (int32_t)lane + 32 * (half * kHalf + u);
-                c[u] = j < hi ? ld_color(io.Xc + w[u], io.pol_col) : (T)0;
+                c[u] = j < hi ? ld_color(io.Xc + (P ? entry_id(w[u]) : w[u]), io.pol_col) : (T)0;
             }
             unsigned nkeep = 0;
 #pragma unroll
@@ -925,8 +946,16 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
                 const bool in = j < hi;
                 const uint32_t col = word_color(c[u]);
                 const bool settled = in && word_settled(c[u]);
+                const int32_t wid = P ? entry_id(w[u]) : w[u];
+                bool pre = false;
+                if constexpr (!P) {
+                    pre = in && col == cv && wid < v;
+                } else if (in && (col == cv || (io.first && !settled))) {
+                    pre = io.first ? precedes(p.prio, wid, v, pv) : w[u] < 0;
+                    if (io.first) w[u] = (int32_t)((uint32_t)wid | (pre ? kPrecBit : 0u));  // the entry kept
+                }
                 if (in) {
-                    if (col == cv && precedes(p.prio, w[u], v, pv)) conflict = true;
+                    if (col == cv && pre) conflict = true;
                     const unsigned idx = col - 1u;
                     // colors 1..64 gather in registers (one warp reduction per chunk); the
                     // rest go to the shared windows, where every lane of the warp would
@@ -1023,7 +1052,7 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 // entries 32 at a time (every task reads at most 1024 entries, so no warp
 // holds up the end of a round); warp gw takes t = gw, gw + W, ... and loads
 // the head of its next task before working on the current one.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc, unsigned gw, unsigned W) {
     __shared__ FlatSmem s_flat[kWarpsPerBlockMax];
@@ -1041,9 +1070,9 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         TaskHead nxt;
         if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
         if (t < nHC) {
-            hub_chunk(p, io, cur, s_flat[wib], maxc, vol);
+            hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
         } else {
-            flat_task(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_flat[wib], maxc, vol);
+            flat_task<T, P>(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_flat[wib], maxc, vol);
         }
         cur = nxt;
     }
@@ -1056,7 +1085,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
 // round reads at most p.tail_volume entries, block 0 runs the remaining rounds
 // alone, separated by block barriers (the other blocks leave): the same
 // synchronous rounds, without the cost of a grid barrier per round.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Params<T> p) {
     RoundState* st = p.st;
     int maxc = 0;
@@ -1092,7 +1121,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
             st->vol[(k + 2) % 3] = 0u;
             if (k - 1 < p.round_cap) p.round_sizes[k - 1] = (int32_t)size;
         }
-        run_pass(p, k, nS, nM, nHC, maxc, gw, W);
+        run_pass<T, P>(p, k, nS, nM, nHC, maxc, gw, W);
         if (tail) {
             __syncthreads();
         } else if (!grid_barrier(st)) {
@@ -1103,11 +1132,11 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
 }
 
 // One pass per launch (loop mode 1): counts come from the host.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __global__ void __launch_bounds__(256, kMinBlocks) round_kernel(Params<T> p, int k, unsigned nS, unsigned nM,
                                                        unsigned nHC) {
     int maxc = 0;
-    run_pass(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+    run_pass<T, P>(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
              (gridDim.x * blockDim.x) >> 5);
     fold_max_color(p.st, maxc);
 }
@@ -1127,14 +1156,14 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
 // Loop mode 2: the rounds as a CUDA graph whose while node repeats
 // graph_round_kernel + graph_cond_kernel on the device.  graph_round_kernel
 // runs round st->graph_round over the counts that the previous pass left.
-template <typename T>
+template <typename T, bool P>  // P: a priority array is given
 __global__ void __launch_bounds__(256, kMinBlocks) graph_round_kernel(Params<T> p) {
     RoundState* st = p.st;
     const int k = __ldcg(&st->graph_round);
     const unsigned* c = st->cnt[k % 3];
     const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nHC = __ldcg(c + 3);
     int maxc = 0;
-    run_pass(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+    run_pass<T, P>(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
              (gridDim.x * blockDim.x) >> 5);
     fold_max_color(st, maxc);
 }
