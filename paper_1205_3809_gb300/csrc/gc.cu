@@ -60,7 +60,23 @@ struct DeviceCache {
     int sms = 0;
     int coop = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t copy = nullptr;                 // host inputs: colidx copies in chunks
+    cudaEvent_t chunk_ev[16] = {};               // one per chunk copied
+    cudaEvent_t start_ev = nullptr;              // orders the copies after the caller's stream
 };
+
+// Host inputs of gc_color_host: colidx goes to the device in chunks of whole
+// 32-vertex tasks on a copy stream, and round 1 runs on each chunk as soon as
+// it has arrived, so the copy overlaps the setup scan and round 1.
+constexpr int kMaxChunks = 16;
+struct HostInput {
+    const int32_t* h_colidx;
+    int32_t* d_colidx;
+    int nchunks;
+    int32_t vb[kMaxChunks + 1];                  // chunk c covers vertices [vb[c], vb[c+1])
+    int64_t eb[kMaxChunks + 1];                  // and adjacency entries [eb[c], eb[c+1])
+};
+
 std::map<int, DeviceCache> g_cache;
 
 #define GC_CUDA(call)                                       \
@@ -74,6 +90,25 @@ std::map<int, DeviceCache> g_cache;
     } while (0)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Queue the chunk copies of a host colidx on the copy stream, after the work
+// already queued on s; chunk c's event fires when it has arrived.
+int issue_host_chunks(DeviceCache& dc, const HostInput& hin, cudaStream_t s) {
+    if (!dc.copy) GC_CUDA(cudaStreamCreateWithFlags(&dc.copy, cudaStreamNonBlocking));
+    if (!dc.start_ev) GC_CUDA(cudaEventCreateWithFlags(&dc.start_ev, cudaEventDisableTiming));
+    for (int c = 0; c < hin.nchunks; ++c)
+        if (!dc.chunk_ev[c]) GC_CUDA(cudaEventCreateWithFlags(&dc.chunk_ev[c], cudaEventDisableTiming));
+    GC_CUDA(cudaEventRecord(dc.start_ev, s));
+    GC_CUDA(cudaStreamWaitEvent(dc.copy, dc.start_ev, 0));
+    for (int c = 0; c < hin.nchunks; ++c) {
+        const int64_t e0 = hin.eb[c], e1 = hin.eb[c + 1];
+        if (e1 > e0)
+            GC_CUDA(cudaMemcpyAsync(hin.d_colidx + e0, hin.h_colidx + e0, (size_t)(e1 - e0) * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, dc.copy));
+        GC_CUDA(cudaEventRecord(dc.chunk_ev[c], dc.copy));
+    }
+    return GC_OK;
+}
 
 int device_cache(DeviceCache** out) {
     int dev = 0;
@@ -214,17 +249,25 @@ int run_rounds_graph(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStr
 }
 
 template <typename T, bool P>
-int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
+int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches,
+                 const HostInput* hin) {
     const int threads = o.block_threads;
     {
-        // one warp task per 32 vertices
-        const int64_t want = ((int64_t)p.n + 255) / 256;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)dc.sms * 8));
-        gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p);
-        GC_CUDA(cudaGetLastError());
+        // one warp task per 32 vertices, per input chunk when the input is still arriving
+        const int nch = hin ? hin->nchunks : 1;
+        for (int c = 0; c < nch; ++c) {
+            const int32_t v0 = hin ? hin->vb[c] : 0, v1 = hin ? hin->vb[c + 1] : p.n;
+            if (hin) GC_CUDA(cudaStreamWaitEvent(s, dc.chunk_ev[c], 0));
+            if (v1 <= v0) continue;
+            const int64_t want = ((int64_t)v1 - v0 + 255) / 256;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)dc.sms * 8));
+            gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p, v0, v1);
+            GC_CUDA(cudaGetLastError());
+            *launches += 1;
+        }
         gc::pass1_long_kernel<T><<<dc.sms * 2, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
-        *launches += 2;
+        *launches += 1;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
     }
     if (o.loop_mode == 2) return run_rounds_graph<T, P>(o, dc, p, s, launches);
@@ -286,8 +329,10 @@ int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_
 // The round kernels are compiled twice: with a priority array (its order
 // kept as a bit in the active lists) and without (index order).
 template <typename T>
-int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches) {
-    return p.prio ? run_rounds_p<T, true>(o, dc, p, s, launches) : run_rounds_p<T, false>(o, dc, p, s, launches);
+int run_rounds(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_t s, int64_t* launches,
+               const HostInput* hin = nullptr) {
+    return p.prio ? run_rounds_p<T, true>(o, dc, p, s, launches, hin)
+                  : run_rounds_p<T, false>(o, dc, p, s, launches, hin);
 }
 
 int normalise(const gc_options* opt, gc_options* o) {
@@ -345,7 +390,8 @@ int validate_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, cud
 
 int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const uint32_t* priority,
                  int32_t* colors_out, int32_t* ncolors, int32_t* rounds, cudaStream_t s,
-                 const gc_options* opt, int32_t* round_sizes, int32_t round_sizes_cap) {
+                 const gc_options* opt, int32_t* round_sizes, int32_t round_sizes_cap,
+                 HostInput* hin = nullptr) {
     gc_options o;
     int rc = normalise(opt, &o);
     if (rc != GC_OK) return rc;
@@ -363,7 +409,12 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     rc = device_cache(&dcp);
     if (rc != GC_OK) return rc;
     DeviceCache& dc = *dcp;
+    if (hin) {
+        rc = issue_host_chunks(dc, *hin, s);
+        if (rc != GC_OK) return rc;
+    }
     if (o.validate) {
+        if (hin) GC_CUDA(cudaStreamWaitEvent(s, dc.chunk_ev[hin->nchunks - 1], 0));
         rc = validate_locked(rowptr, colidx, n, s, dc, &launches);
         if (rc != GC_OK) return rc;
     }
@@ -455,11 +506,11 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
         if (bits == 16) {
             Params<uint16_t> p;
             fill(p);
-            rc = run_rounds(o, dc, p, s, &launches);
+            rc = run_rounds(o, dc, p, s, &launches, hin);
         } else {
             Params<int32_t> p;
             fill(p);
-            rc = run_rounds(o, dc, p, s, &launches);
+            rc = run_rounds(o, dc, p, s, &launches, hin);
         }
         if (rc != GC_OK) return rc;
         if (bits == 32) break;
@@ -770,7 +821,7 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
     {
         const int64_t want = (b.N + 255) / 256;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b.sms * 8));
-        gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p);
+        gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p, 0, (int32_t)b.N);
         GC_CUDA(cudaGetLastError());
         gc::pass1_long_kernel<T><<<b.sms * 2, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
@@ -1052,9 +1103,26 @@ int gc_color_host(const int32_t* rowptr, const int32_t* colidx, int32_t n, const
     uint32_t* d_pr = priority ? (uint32_t*)(base + b_rp + b_ci) : nullptr;
     int32_t* d_co = (int32_t*)(base + b_rp + b_ci + b_pr);
     GC_CUDA(cudaMemcpyAsync(d_rp, rowptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s));
-    if (nnz > 0) GC_CUDA(cudaMemcpyAsync(d_ci, colidx, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
     if (priority) GC_CUDA(cudaMemcpyAsync(d_pr, priority, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    rc = color_locked(d_rp, d_ci, n, d_pr, d_co, ncolors, rounds, s, opt, nullptr, 0);
+    // colidx in chunks of about equal size, cut at multiples of 32 vertices
+    HostInput hin;
+    hin.h_colidx = colidx;
+    hin.d_colidx = d_ci;
+    hin.nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(8, nnz / (1 << 20)));
+    hin.vb[0] = 0;
+    hin.eb[0] = 0;
+    for (int c = 1; c < hin.nchunks; ++c) {
+        const int64_t target = nnz * c / hin.nchunks;
+        int32_t v = (int32_t)(std::lower_bound(rowptr, rowptr + n + 1, (int32_t)target) - rowptr);
+        v = std::max(hin.vb[c - 1], std::min(n, v & ~31));
+        hin.vb[c] = v;
+        // (clamped, so the copies stay inside both buffers even for a malformed
+        // rowptr, which the setup scan then rejects)
+        hin.eb[c] = std::min<int64_t>(nnz, std::max<int64_t>(hin.eb[c - 1], rowptr[v]));
+    }
+    hin.vb[hin.nchunks] = n;
+    hin.eb[hin.nchunks] = nnz;
+    rc = color_locked(d_rp, d_ci, n, d_pr, d_co, ncolors, rounds, s, opt, nullptr, 0, &hin);
     if (rc != GC_OK) return rc;
     GC_CUDA(cudaMemcpyAsync(colors_out, d_co, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     GC_CUDA(cudaStreamSynchronize(s));
@@ -1129,6 +1197,10 @@ int gc_release(void) {
         if (kv.second.host) cudaFreeHost(kv.second.host);
         for (int i = 0; i < 4; ++i)
             if (kv.second.ev[i]) cudaEventDestroy(kv.second.ev[i]);
+        for (int i = 0; i < kMaxChunks; ++i)
+            if (kv.second.chunk_ev[i]) cudaEventDestroy(kv.second.chunk_ev[i]);
+        if (kv.second.start_ev) cudaEventDestroy(kv.second.start_ev);
+        if (kv.second.copy) cudaStreamDestroy(kv.second.copy);
     }
     g_cache.clear();
     g_last.valid = 0;

@@ -499,25 +499,27 @@ __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
     return nl;
 }
 
-// Round 1 on 32 consecutive vertices per task.  Their adjacency entries
+// Round 1 on 32 consecutive vertices per task, over vertices [v_begin, v_end)
+// (v_begin a multiple of 32; the host may launch it per range as the input
+// arrives).  Their adjacency entries
 // (rows of degree <= kPass1Flat) are read as one flat, coalesced range;
 // lane l of batch u handles flat entry F0 + 32u + l, finds its row by a
 // binary search over the rows' running totals, and the per-row conflict
 // flag is gathered from the batch ballot.  Longer rows go to
 // pass1_long_kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
+__global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin, int32_t v_end) {
     const unsigned lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t ntasks = ((int64_t)p.n + 31) / 32;
+    const int64_t ntasks = ((int64_t)v_end - v_begin + 31) / 32;
     const NextLists nl = pass1_next(p);
     const uint64_t pol_adj = policy_evict_first();
     int maxc = 0;
     unsigned vol = 0;
     for (int64_t t = gw; t < ntasks; t += W) {
-        const int64_t vv = t * 32 + lane;
-        const bool valid = vv < p.n;
+        const int64_t vv = (int64_t)v_begin + t * 32 + lane;
+        const bool valid = vv < v_end;
         const int32_t v = valid ? (int32_t)vv : 0;
         const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
         const int32_t d = valid ? __ldg(p.rowptr + v + 1) - b : 0;
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p) {
             for (int u = 0; u < 4; ++u) {
                 const int32_t f = F0 + 32 * u + (int32_t)lane;
                 const uint32_t opv = __shfl_sync(kFull, pv, own[u]);
-                const bool h = f < D && precedes(p.prio, w[u], (int32_t)(t * 32 + own[u]), opv);
+                const bool h = f < D && precedes(p.prio, w[u], (int32_t)(v_begin + t * 32 + own[u]), opv);
                 const unsigned ballot = __ballot_sync(kFull, h);
                 const int32_t lo = max(0, min(32, off - (F0 + 32 * u)));
                 const int32_t hi = max(0, min(32, off + eff - (F0 + 32 * u)));
@@ -746,7 +748,7 @@ __device__ __forceinline__ void st_stream(int32_t* a, int32_t x, uint64_t pol) {
 // vertex's running write position.  Afterwards each lane decides its own
 // vertex.
 template <typename T, bool P>  // P: a priority array is given
-__device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en, int bin,
+__device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& io, int4 en,
                                           FlatSmem& sm, int& maxc, unsigned& vol) {
     const unsigned lane = lane_id();
     const bool valid = en.x >= 0;
@@ -895,7 +897,6 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     const int nb = bin_of(kept, p.s_max, p.m_max);
     warp_append(conflict && nb == kBinS, ne, io.next.S, &io.next.cnt[kBinS]);
     warp_append(conflict && nb == kBinM, ne, io.next.M, &io.next.cnt[kBinM]);
-    (void)bin;
     __syncwarp();
 }
 
@@ -1072,7 +1073,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         if (t < nHC) {
             hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
         } else {
-            flat_task<T, P>(p, io, cur.e, t - nHC < tM ? kBinM : kBinS, s_flat[wib], maxc, vol);
+            flat_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
         }
         cur = nxt;
     }
