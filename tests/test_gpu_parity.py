@@ -170,6 +170,28 @@ def test_host_entry_point(gcpkg):
     assert np.array_equal(res.colors, ref.colors) and res.ncolors == ref.ncolors
 
 
+@pytest.mark.parametrize("scale,opts", [(18, None), (19, {"validate": 1}), (19, {"loop_mode": 2})])
+def test_host_entry_point_in_chunks(gcpkg, scale, opts):
+    """Host inputs large enough that colidx goes over in several chunks, round 1
+    running on each as it arrives (8 chunks at scale 19)."""
+    g = gg.rmat(scale, 8, gg.RMAT_B, 6)
+    assert g.nnz >= 2 << 20
+    res = gcpkg.color_host(g.rowptr, g.colidx, options=opts)
+    ref = oracle.iterative(g.rowptr, g.colidx)
+    assert (res.ncolors, res.rounds) == (ref.ncolors, ref.rounds)
+    assert np.array_equal(res.colors, ref.colors)
+    prio = (gg.draws(4, 5, g.n) >> np.uint64(44)).astype(np.uint32)
+    res = gcpkg.color_host(g.rowptr, g.colidx, prio, options=opts)
+    ref = oracle.iterative(g.rowptr, g.colidx, prio)
+    assert np.array_equal(res.colors, ref.colors) and res.ncolors == ref.ncolors
+
+
+def test_host_entry_point_edgeless(gcpkg):
+    g = gg.edgeless(100)
+    res = gcpkg.color_host(g.rowptr, g.colidx)
+    assert res.ncolors == 1 and res.rounds == 1 and np.all(res.colors == 1)
+
+
 def test_validation_rejects_bad_graphs(gcpkg):
     g = gg.gnm(500, 2000, 3)
     assert gcpkg.validate_csr(_dev(g.rowptr), _dev(g.colidx)) == gcpkg.GC_OK
