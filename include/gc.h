@@ -271,7 +271,9 @@ int gc_batch_create(const int32_t* rowptr_cat, const int32_t* colidx_cat, const 
 
 /* gc_batch_run - enqueue one coloring of the planned batch on `stream`:
  * memsets and kernels only (no allocation, no host synchronisation), so it
- * may be captured into a CUDA graph.  Read the status with gc_batch_status. */
+ * may be captured into a CUDA graph.  Read the status with gc_batch_status.
+ * Runs of one plan use its one workspace: they must not overlap on the GPU
+ * (issue them on one stream, or order the streams). */
 int gc_batch_run(gc_batch* plan, void* stream);
 
 /* gc_batch_launch_graph - the first call captures gc_batch_run into a CUDA
