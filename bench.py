@@ -58,6 +58,13 @@ def log(*a):
 def cpu_model() -> str:
     """The host CPU's model string, as far as the OS reports it."""
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
@@ -65,7 +72,7 @@ def cpu_model() -> str:
                     return line.split(":", 1)[1].strip()
     except OSError:
         pass
-    return platform.processor() or "unknown"
+    return platform.processor() or platform.machine() or "unknown"
 
 
 def dist_env():

@@ -1,6 +1,7 @@
 """Write tests/golden/fullsize.json: the oracle's result on the full-size
-synthetic workloads, stored as a SHA-256 of the int32 colors plus ncolors,
-rounds and |U_r| of every round.  Calls only graphgen/ and oracle/.
+synthetic workloads (index priority, and the shipped learned priority with
+keys the oracle computes itself), stored as a SHA-256 of the int32 colors plus
+ncolors, rounds and |U_r| of every round.  Calls only graphgen/ and oracle/.
 
     python tests/golden/make_fullsize.py [name ...]
 """
@@ -30,6 +31,18 @@ WORKLOADS = {
 }
 
 
+# learned priority: the shipped network's keys (computed by the oracle), then the same rounds
+LEARNED = {"rmat_b_s24_seed3_learned": "rmat_b_s24_seed3"}
+
+
+def learned_keys(g):
+    import json as _json
+    from oracle import learned as L
+    path = os.path.join(ROOT, "paper_1205_3809_gb300", "priority_mlp_rmat_g.json")
+    params = np.asarray(_json.load(open(path))["params"], dtype=np.float32)
+    return L.learned_keys(g.rowptr, g.colidx, params)
+
+
 def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).astype("<i4").tobytes()).hexdigest()
 
@@ -38,9 +51,10 @@ def main(names):
     path = os.path.join(ROOT, "tests", "golden", "fullsize.json")
     out = json.load(open(path)) if os.path.exists(path) else {}
     for name in names:
-        g = WORKLOADS[name]()
+        g = WORKLOADS[LEARNED.get(name, name)]()
         t = time.time()
-        r = oracle.iterative(g.rowptr, g.colidx)
+        keys = learned_keys(g) if name in LEARNED else None
+        r = oracle.iterative(g.rowptr, g.colidx, keys)
         out[name] = {
             "n": g.n, "nnz": g.nnz,
             "graph_sha256": hashlib.sha256(g.rowptr.astype("<i4").tobytes()
@@ -56,4 +70,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(WORKLOADS))
+    main(sys.argv[1:] or list(WORKLOADS) + list(LEARNED))

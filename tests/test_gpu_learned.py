@@ -227,10 +227,21 @@ def test_committed_model_on_rmat_g_scale23(gcpkg):
 
 def test_committed_model_on_rmat_b_scale24(gcpkg):
     """The shipped network on the skewed R-MAT-B scale 24 graph (seed 3), a family it
-    was not trained on: a valid coloring with no more colors than index priority."""
+    was not trained on: a valid coloring with no more colors than index priority, and
+    the oracle's result under the oracle's own keys (stored by make_fullsize.py)."""
+    import hashlib
+    import json
+    import os
     g = gg.rmat(24, 8, gg.RMAT_B, 3)
     rp, ci = _dev(g.rowptr), _dev(g.colidx)
     plain = gcpkg.color(rp, ci)
-    learned = gcpkg.color_learned(rp, ci)
+    learned = gcpkg.color_learned(rp, ci, round_sizes=True)
     assert learned.ncolors <= plain.ncolors, (learned.ncolors, plain.ncolors)
-    _valid(g, learned.colors.cpu().numpy())
+    colors = learned.colors.cpu().numpy()
+    _valid(g, colors)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize.json")
+    exp = json.load(open(path)).get("rmat_b_s24_seed3_learned")
+    if exp is not None:
+        assert (learned.ncolors, learned.rounds) == (exp["ncolors"], exp["rounds"])
+        assert learned.round_sizes.tolist() == exp["round_sizes"]
+        assert hashlib.sha256(colors.astype("<i4").tobytes()).hexdigest() == exp["colors_sha256"]
