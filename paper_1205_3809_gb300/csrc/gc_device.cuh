@@ -784,8 +784,9 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     sm.vid[lane] = v;
     int32_t kept = 0;  // entries of this lane's vertex written for the next round
     __syncwarp();
+    const int32_t b_off = b - off;  // row start minus flat offset: entry f of this row is at b_off + f
     for (int32_t F0 = 0; F0 < D; F0 += 32 * kFlatBatches) {
-        int32_t w[kFlatBatches], own[kFlatBatches], ob[kFlatBatches], oo[kFlatBatches];
+        int32_t w[kFlatBatches], own[kFlatBatches], seglo[kFlatBatches];
 #pragma unroll
         for (int u = 0; u < kFlatBatches; ++u) {
             const int32_t base = F0 + 32 * u;
@@ -794,12 +795,15 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             const int32_t rel = off - base;
             const unsigned before = __popc(__ballot_sync(kFull, len > 0 && rel < 0));
             const unsigned starts = __reduce_or_sync(kFull, (len > 0 && rel >= 0 && rel < 32) ? (1u << rel) : 0u);
-            const unsigned rank = before + __popc(starts & (0xffffffffu >> (31 - lane)));
+            const unsigned upto = starts & (0xffffffffu >> (31 - lane));
+            const unsigned rank = before + __popc(upto);
             const int o = (f < D && rank > 0) ? (int)sm.lane_of[rank - 1] : 0;
             own[u] = o;
-            ob[u] = __shfl_sync(kFull, b, o);
-            oo[u] = __shfl_sync(kFull, off, o);
-            w[u] = f < D ? ld_row(io.rin + ob[u] + (f - oo[u]), io.pol_row) : 0;
+            // first lane of my owner's entries in this batch: the last row start at or
+            // before this lane, or 0 if the row began in an earlier batch
+            seglo[u] = upto ? 31 - __clz(upto) : 0;
+            const int32_t rb = __shfl_sync(kFull, b_off, o);
+            w[u] = f < D ? ld_row(io.rin + rb + f, io.pol_row) : 0;
         }
         T c[kFlatBatches];
 #pragma unroll
@@ -813,7 +817,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             const int32_t f = base + (int32_t)lane;
             const int o = own[u];
             const uint32_t ocv = __shfl_sync(kFull, cv, o);
-            const int32_t okept = __shfl_sync(kFull, kept, o);
+            const int32_t wbase = __shfl_sync(kFull, b + kept, o);  // next free slot of the owner's list
             const bool in = f < D;
             const uint32_t col = word_color(c[u]);
             const bool settled = in && word_settled(c[u]);
@@ -842,10 +846,9 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
             // survivors: copy to the next round's list, in order within each vertex
             const bool keep = in && !settled;
             const unsigned kb = __ballot_sync(kFull, keep);
-            const int32_t seglo = max(0, oo[u] - base);  // first lane of my vertex in this batch
-            const unsigned below = kb & ((1u << lane) - 1u) & ~((1u << seglo) - 1u);
+            const unsigned below = kb & ((1u << lane) - 1u) & ~((1u << seglo[u]) - 1u);
             if (keep)
-                st_stream(io.rout + ob[u] + okept + __popc(below),
+                st_stream(io.rout + wbase + __popc(below),
                           (P && io.first) ? (int32_t)((uint32_t)wid | (pre ? kPrecBit : 0u)) : w[u],
                           io.pol_row);
             // my vertex's lanes in this batch: [lo, hi)
