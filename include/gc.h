@@ -287,6 +287,14 @@ int gc_batch_launch_graph(gc_batch* plan, void* stream);
  * or GC_ERR_TIMEOUT. */
 int gc_batch_status(gc_batch* plan, void* stream, int32_t* max_rounds, int32_t* max_colors);
 
+/* gc_batch_features - the six gc_features features of every vertex of the
+ * batch (features: voff[G] * 6 floats, device), from the plan's union graph
+ * rebuilt from the current colidx_cat; graph g's rows at features[6*voff[g]..].
+ * A vertex's features depend only on its own graph.  With gc_mlp_forward and
+ * gc_priority_keys this gives the learned priority of every graph at once,
+ * to be written into the priority array the plan was created with. */
+int gc_batch_features(gc_batch* plan, float* features, void* stream);
+
 /* gc_batch_destroy - free the plan (waits for the device); NULL is a no-op. */
 int gc_batch_destroy(gc_batch* plan);
 

@@ -39,7 +39,7 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
-            "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async")
+            "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async", "gc_batch_features")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -130,6 +130,8 @@ def _load():
         lib.gc_batch_destroy.argtypes = [vp]
         lib.gc_batch_workspace_bytes.argtypes = [vp]
         lib.gc_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.gc_batch_features.argtypes = [vp, vp, vp]
+        lib.gc_batch_features.restype = ctypes.c_int
         lib.gc_batch_launch_count.argtypes = [vp]
         lib.gc_batch_launch_count.restype = ctypes.c_int64
         for f in (lib.gc_batch_create, lib.gc_batch_run, lib.gc_batch_launch_graph, lib.gc_batch_status,
@@ -580,6 +582,27 @@ class Batch:
             _check(self._lib.gc_batch_status(self._h, _stream_handle(stream, self.device), ctypes.byref(r),
                                              ctypes.byref(c)), "gc_batch_status")
         return int(r.value), int(c.value)
+
+    def features(self, *, out=None, stream=None):
+        """float32 [voff[G], 6] features of every vertex of the batch (``gc_batch_features``)."""
+        import torch
+        n = int(self.colors.numel())
+        if out is None:
+            out = torch.empty((n, 6), dtype=torch.float32, device=self.device)
+        fp = _dev_ptr(out, torch.float32, "out", n * 6)
+        with torch.cuda.device(self.device):
+            _check(self._lib.gc_batch_features(self._h, fp, _stream_handle(stream, self.device)),
+                   "gc_batch_features")
+        return out
+
+    def learned_priority(self, params=None, *, out=None, stream=None):
+        """Keys of the learned priority for every graph of the batch, written into ``out``
+        (pass the priority tensor the plan was created with); the trained model when
+        params is None."""
+        if params is None:
+            params = load_priority_model(device=self.device)
+        scores = mlp_forward(params, self.features(stream=stream), stream=stream)
+        return priority_keys(scores, out=out, stream=stream)
 
     @property
     def workspace_bytes(self) -> int:

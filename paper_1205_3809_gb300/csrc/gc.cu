@@ -783,28 +783,36 @@ struct gc_batch {
 
 namespace {
 
+// Rebuild the union colidx from the caller's colidx_cat (local ids -> union ids).
+int batch_rebase(gc_batch& b, cudaStream_t s, int64_t* launches) {
+    char* base = (char*)b.ws;
+    gc::BatchFlags* fl = (gc::BatchFlags*)(base + b.off_flags);
+    GC_CUDA(cudaMemsetAsync(&fl->bad_colidx, 0, sizeof(int), s));
+    if (b.NNZ == 0) return GC_OK;
+    const int64_t spans = (b.NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b.sms * 8));
+    gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(b.colidx_cat, (const int64_t*)(base + b.off_voff),
+                                                 (const int64_t*)(base + b.off_eoff), b.G, b.NNZ,
+                                                 (int32_t*)(base + b.off_colidx), fl);
+    GC_CUDA(cudaGetLastError());
+    ++*launches;
+    return GC_OK;
+}
+
 template <typename T>
 int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
     char* base = (char*)b.ws;
     const int64_t* voff = (const int64_t*)(base + b.off_voff);
-    const int64_t* eoff = (const int64_t*)(base + b.off_eoff);
     int32_t* rowptr_g = (int32_t*)(base + b.off_rowptr);
     int32_t* colidx_g = (int32_t*)(base + b.off_colidx);
     int32_t* settle = (int32_t*)(base + b.off_settle);
-    gc::BatchFlags* fl = (gc::BatchFlags*)(base + b.off_flags);
     RoundState* st = (RoundState*)(base + b.L.st);
     GC_CUDA(cudaMemsetAsync(st, 0, sizeof(RoundState), s));
     GC_CUDA(cudaMemsetAsync(base + b.L.rv, 0, (size_t)b.round_cap * sizeof(unsigned long long), s));
     GC_CUDA(cudaMemsetAsync(base + b.L.hubs, 0, (size_t)b.hs.cap[gc::kBinH] * sizeof(gc::HubRecord), s));
-    GC_CUDA(cudaMemsetAsync(&fl->bad_colidx, 0, sizeof(int), s));
     int64_t launches = 0;
-    if (b.NNZ > 0) {
-        const int64_t spans = (b.NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b.sms * 8));
-        gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(b.colidx_cat, voff, eoff, b.G, b.NNZ, colidx_g, fl);
-        GC_CUDA(cudaGetLastError());
-        ++launches;
-    }
+    int rc = batch_rebase(b, s, &launches);
+    if (rc != GC_OK) return rc;
     Params<T> p;
     p.rowptr = rowptr_g;
     p.colidx = colidx_g;
@@ -1252,6 +1260,22 @@ int gc_batch_create(const int32_t* rowptr_cat, const int32_t* colidx_cat, const 
 int gc_batch_run(gc_batch* plan, void* stream) {
     if (!plan) return GC_ERR_INVALID;
     return batch_enqueue(*plan, (cudaStream_t)stream);
+}
+
+int gc_batch_features(gc_batch* plan, float* features, void* stream) {
+    if (!plan) return GC_ERR_INVALID;
+    gc_batch& b = *plan;
+    int dev = -1;
+    GC_CUDA(cudaGetDevice(&dev));
+    if (dev != b.device) return GC_ERR_INVALID;
+    if (b.G == 0 || b.N == 0) return GC_OK;
+    if (!features) return GC_ERR_INVALID;
+    int64_t launches = 0;
+    const int rc = batch_rebase(b, (cudaStream_t)stream, &launches);
+    if (rc != GC_OK) return rc;
+    char* base = (char*)b.ws;
+    return gc_features((const int32_t*)(base + b.off_rowptr), (const int32_t*)(base + b.off_colidx), (int32_t)b.N,
+                       features, stream);
 }
 
 int gc_batch_launch_graph(gc_batch* plan, void* stream) {

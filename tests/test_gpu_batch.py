@@ -208,3 +208,28 @@ def test_autotune_batch(gcpkg, tmp_path, monkeypatch):
     b.run(graph=True)
     b.status()
     _check(gs, b, voff)
+
+
+def test_learned_priority_on_a_batch(gcpkg):
+    """Features on the union graph equal each graph's own features, so the learned
+    keys of a batch are each graph's learned keys and every graph gets the oracle's
+    learned coloring."""
+    from oracle import learned as L
+    gs = _small_mix()[:40]
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+    keys = torch.zeros(int(voff[-1]), dtype=torch.int32, device="cuda")
+    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, keys)
+    params = gcpkg.load_priority_model()
+    b.learned_priority(_dev(params), out=keys)
+    f = b.features().cpu().numpy()
+    b.run(graph=True)
+    b.status()
+    got_keys = keys.cpu().numpy().view(np.uint32)
+    want = []
+    for i, g in enumerate(gs):
+        assert np.array_equal(f[voff[i]:voff[i + 1]].view(np.uint32),
+                              L.features(g.rowptr, g.colidx).view(np.uint32)), i
+        k = L.learned_keys(g.rowptr, g.colidx, params)
+        assert np.array_equal(got_keys[voff[i]:voff[i + 1]], k), i
+        want.append(k)
+    _check(gs, b, voff, keys=want)
