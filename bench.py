@@ -221,22 +221,33 @@ def gathers_rounds(vols):
     return int(sum(int(x) for x in vols[1:]))
 
 
-def load_traffic(kernel_src):
-    """Per-launch DRAM bytes of the rounds kernel from the committed ncu summary,
-    or None if the kernel source changed since it was captured."""
+def load_profile_fields(kernel_src):
+    """Per-launch counters of the rounds kernel from the committed ncu summary
+    (`- key: value` lines), or {} if the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "rounds_persistent_kernel_rmat_b.md")
     if not os.path.exists(path):
-        return None
+        return {}
     want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_source_sha256") != want:
-        return None
+    return fields if fields.get("kernel_source_sha256") == want else {}
+
+
+def load_traffic(kernel_src):
+    """Per-launch DRAM bytes of the rounds kernel (full size), or None."""
     try:
-        return int(fields["traffic_bytes_per_launch_full_size"])
+        return int(load_profile_fields(kernel_src)["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def load_l2_sectors(kernel_src):
+    """Per-launch L2 sectors of the rounds kernel at full size (a one-pass capture), or None."""
+    try:
+        return int(load_profile_fields(kernel_src)["l2_sectors_per_launch_full_size"])
     except (KeyError, ValueError):
         return None
 
@@ -321,6 +332,7 @@ def run_ours(args):
     traffic = load_traffic(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
     gathers = gathers_rounds(vols)
     gather_rate = gathers / (kms / 1e3) / 1e9
+    sectors = load_l2_sectors(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
 
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
@@ -384,7 +396,12 @@ def run_ours(args):
                          "algorithmic_bytes": alg_bytes, "kernel_ms": kms,
                          "l2_gathers": {"count": gathers, "achieved_G_per_s": gather_rate,
                                         "ceiling_G_per_s": L2_GATHER_CEILING,
-                                        "frac": gather_rate / L2_GATHER_CEILING}},
+                                        "frac": gather_rate / L2_GATHER_CEILING},
+                         "l2_sectors": None if sectors is None else {
+                             "count": sectors, "achieved_G_per_s": sectors / (kms / 1e3) / 1e9,
+                             "ceiling_G_per_s": L2_GATHER_CEILING,
+                             "frac": sectors / (kms / 1e3) / 1e9 / L2_GATHER_CEILING,
+                             "source": "lts__t_sectors.sum of one full-size launch (profiles/)"}},
             "cpu_baseline": cpu,
             "learned": learned,
             "asynchronous": asynchronous,
