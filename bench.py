@@ -222,19 +222,30 @@ def gathers_rounds(vols):
     return int(sum(int(x) for x in vols[1:]))
 
 
+def kernel_code_hash(path: str) -> str:
+    """SHA-256 of a CUDA source's code: comments and blank lines removed, so a
+    change to the text around the code does not void a profile of the code."""
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def load_profile_fields(kernel_src):
     """Per-launch counters of the rounds kernel from the committed ncu summary
     (`- key: value` lines), or {} if the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "rounds_persistent_kernel_rmat_b.md")
     if not os.path.exists(path):
         return {}
-    want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    want = kernel_code_hash(kernel_src)
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    return fields if fields.get("kernel_source_sha256") == want else {}
+    return fields if fields.get("kernel_code_sha256") == want else {}
 
 
 def load_traffic(kernel_src):

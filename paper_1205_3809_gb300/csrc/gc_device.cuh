@@ -39,6 +39,14 @@
 //     and the warp that finishes the last chunk decides.
 // Tasks are dealt to warps round-robin; no block-wide barrier is taken
 // inside a round.
+//
+// Priority: the round kernels are instantiated for index priority (the test
+// is one compare) and for a priority array, whose (key, index) order round 2
+// evaluates once per kept neighbour and stores in bit 31 of the active-list
+// entry.  Loops: all rounds in one cooperative launch with a bounded grid
+// barrier (optionally handing the last rounds to block 0), one launch per
+// round, or a CUDA graph whose while node repeats a round kernel and a
+// one-thread condition kernel.
 #pragma once
 
 #include <cuda_runtime.h>
