@@ -217,6 +217,24 @@ def algorithmic_bytes_rounds(sizes, vols, elem):
     return total
 
 
+def algorithmic_bytes_batch(N, NNZ, sizes, vols, elem):
+    """Bytes one batched run must move, all of its kernels together.
+
+    Rebase: colidx read and written (8*NNZ).  Pass 1 (round 1 and round 2's
+    Phase 1): rowptr 4(N+1) and colidx 4*NNZ read; both color buffers
+    2*elem*N, final color and settle round 8 per vertex settled in round 1,
+    a tuple 16|U_2| written.  Rounds k >= 2: algorithmic_bytes_rounds, plus
+    the settle round 4 per vertex they settle.  Reduce: final colors and
+    settle rounds read, 8N.
+    """
+    u2 = int(sizes[1]) if len(sizes) > 1 else 0
+    rebase = 8 * NNZ
+    pass1 = 4 * (N + 1) + 4 * NNZ + 2 * elem * N + 8 * (N - u2) + 16 * u2
+    rounds = algorithmic_bytes_rounds(sizes, vols, elem) + 4 * u2
+    reduce = 8 * N
+    return rebase + pass1 + rounds + reduce
+
+
 def gathers_rounds(vols):
     """Random neighbour-color reads of the rounds kernel (one per active entry)."""
     return int(sum(int(x) for x in vols[1:]))
@@ -546,6 +564,12 @@ def run_batched(args):
     max_rounds, max_colors = b.status()
     ms = [a.elapsed_time(e) for a, e in evs]
     total_s = sum(ms) / 1e3
+    sizes, vols, bits = b.round_stats()
+    N, NNZ = int(voff[-1]), int(eoff[-1])
+    alg_bytes = algorithmic_bytes_batch(N, NNZ, sizes, vols, bits // 8)
+    run_s = total_s / len(evs)
+    peak, peak_kind = peaks()
+    gathers = gathers_rounds(vols)
     # end to end: host buffers in, colors and per-graph counts out
     h_rp, h_ci = torch.from_numpy(rp).pin_memory(), torch.from_numpy(ci).pin_memory()
     h_col = torch.empty(int(voff[-1]), dtype=torch.int32).pin_memory()
@@ -575,6 +599,14 @@ def run_batched(args):
                    "options": best, "max_rounds": max_rounds, "max_colors": max_colors,
                    "workspace_bytes": b.workspace_bytes,
                    "l2": "inputs larger than L2 and L2 flushed (256 MB write) before every step"},
+        "roofline": {"bound": "hbm", "kernel": "whole run (rebase, pass 1, rounds, reduce; one CUDA graph)",
+                     "achieved": alg_bytes / run_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": alg_bytes / run_s / 1e9 / peak, "traffic": None,
+                     "algorithmic_bytes": alg_bytes, "run_ms": 1e3 * run_s, "color_state_bits": bits,
+                     "round_sizes": [int(x) for x in sizes],
+                     "l2_gathers": {"count": gathers, "achieved_G_per_s": gathers / run_s / 1e9,
+                                    "ceiling_G_per_s": L2_GATHER_CEILING,
+                                    "frac": gathers / run_s / 1e9 / L2_GATHER_CEILING}},
         "autotune": [{"options": o, "ms": round(t_, 3)} for o, t_ in table],
         "e2e": {"value": m_total / (statistics.mean(e_ms) / 1e3), "unit": "edges/s",
                 "h2d_bytes_per_step": 4 * (rp.size + ci.size), "d2h_bytes_per_step": 4 * (int(voff[-1]) + len(gs)),

@@ -295,6 +295,15 @@ int gc_batch_status(gc_batch* plan, void* stream, int32_t* max_rounds, int32_t* 
  * to be written into the priority array the plan was created with. */
 int gc_batch_features(gc_batch* plan, float* features, void* stream);
 
+/* gc_batch_round_stats - after a run (waits for `stream`): |U_r| over the whole
+ * batch (sizes[r-1], host array of `cap`) and the active adjacency entries
+ * round r read (volumes[r-1]; round 1 reads every row) for the first
+ * min(rounds, cap, 4096) rounds, and the plan's color-state width in bits
+ * (state_bits, 16 or 32).  Any output may be NULL.  Returns that round count,
+ * or a gc_status (GC_ERR_INVALID for a NULL plan or cap < 0). */
+int gc_batch_round_stats(gc_batch* plan, int32_t* sizes, int64_t* volumes, int32_t cap, int32_t* state_bits,
+                         void* stream);
+
 /* gc_batch_destroy - free the plan (waits for the device); NULL is a no-op. */
 int gc_batch_destroy(gc_batch* plan);
 

@@ -39,7 +39,8 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
-            "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async", "gc_batch_features")
+            "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async", "gc_batch_features",
+            "gc_batch_round_stats")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -131,6 +132,8 @@ def _load():
         lib.gc_batch_workspace_bytes.argtypes = [vp]
         lib.gc_batch_workspace_bytes.restype = ctypes.c_size_t
         lib.gc_batch_features.argtypes = [vp, vp, vp]
+        lib.gc_batch_round_stats.argtypes = [vp, vp, vp, i32, vp, vp]
+        lib.gc_batch_round_stats.restype = ctypes.c_int
         lib.gc_batch_features.restype = ctypes.c_int
         lib.gc_batch_launch_count.argtypes = [vp]
         lib.gc_batch_launch_count.restype = ctypes.c_int64
@@ -603,6 +606,21 @@ class Batch:
             params = load_priority_model(device=self.device)
         scores = mlp_forward(params, self.features(stream=stream), stream=stream)
         return priority_keys(scores, out=out, stream=stream)
+
+    def round_stats(self, cap: int = 4096, stream=None):
+        """(sizes, volumes, state_bits) of the last run over the whole batch
+        (``gc_batch_round_stats``): |U_r| and the active entries round r read."""
+        import torch
+        sizes = np.zeros(cap, np.int32)
+        vols = np.zeros(cap, np.int64)
+        bits = ctypes.c_int32(0)
+        with torch.cuda.device(self.device):
+            m = int(self._lib.gc_batch_round_stats(self._h, ctypes.c_void_p(sizes.ctypes.data),
+                                                   ctypes.c_void_p(vols.ctypes.data), cap, ctypes.byref(bits),
+                                                   _stream_handle(stream, self.device)))
+        if m < 0:
+            raise GcError(m, "gc_batch_round_stats")
+        return sizes[:m].copy(), vols[:m].copy(), int(bits.value)
 
     @property
     def workspace_bytes(self) -> int:

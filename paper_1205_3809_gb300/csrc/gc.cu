@@ -1262,6 +1262,35 @@ int gc_batch_run(gc_batch* plan, void* stream) {
     return batch_enqueue(*plan, (cudaStream_t)stream);
 }
 
+int gc_batch_round_stats(gc_batch* plan, int32_t* sizes, int64_t* volumes, int32_t cap, int32_t* state_bits,
+                         void* stream) {
+    if (!plan || cap < 0) return GC_ERR_INVALID;
+    gc_batch& b = *plan;
+    if (state_bits) *state_bits = b.bits;
+    if (b.G == 0 || b.N == 0 || cap == 0) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)b.ws;
+    RoundState hst;
+    GC_CUDA(cudaMemcpyAsync(&hst, base + b.L.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    const int32_t m = (int32_t)std::min<int64_t>({(int64_t)hst.rounds, (int64_t)cap, b.round_cap});
+    if (m <= 0) return 0;
+    if (sizes) {
+        sizes[0] = (int32_t)b.N;
+        if (m > 1)
+            GC_CUDA(cudaMemcpyAsync(sizes + 1, (const int32_t*)(base + b.L.rs) + 1, (size_t)(m - 1) * 4,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    if (volumes) {
+        volumes[0] = b.NNZ;
+        if (m > 1)
+            GC_CUDA(cudaMemcpyAsync(volumes + 1, (const unsigned long long*)(base + b.L.rv) + 1, (size_t)(m - 1) * 8,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    GC_CUDA(cudaStreamSynchronize(s));
+    return m;
+}
+
 int gc_batch_features(gc_batch* plan, float* features, void* stream) {
     if (!plan) return GC_ERR_INVALID;
     gc_batch& b = *plan;

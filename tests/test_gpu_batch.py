@@ -233,3 +233,30 @@ def test_learned_priority_on_a_batch(gcpkg):
         assert np.array_equal(got_keys[voff[i]:voff[i + 1]], k), i
         want.append(k)
     _check(gs, b, voff, keys=want)
+
+
+def test_round_stats(gcpkg):
+    """Per-round telemetry of a batch run: |U_r| over the batch is the sum of
+    every graph's own |U_r| (the oracle's), round 1 reads every entry, round 2
+    every row of U_2, and later rounds no more than the rows of U_r."""
+    gs = _small_mix()
+    b, voff = _plan(gcpkg, gs)
+    b.run(graph=True)
+    mr, _ = b.status()
+    sizes, vols, bits = b.round_stats()
+    assert bits in (16, 32) and len(sizes) == len(vols) == mr
+    want = np.zeros(mr, np.int64)
+    deg_in_round = np.zeros(mr, np.int64)
+    for g in gs:
+        ref = oracle.iterative(g.rowptr, g.colidx)
+        want[:len(ref.round_sizes)] += ref.round_sizes
+        for k in range(1, mr + 1):
+            deg_in_round[k - 1] += int(g.degrees[ref.settle_round >= k].sum())
+    assert sizes.tolist() == want.tolist()
+    assert vols[0] == sum(int(g.rowptr[-1]) for g in gs)
+    if mr >= 2:
+        assert vols[1] == deg_in_round[1]
+    assert np.all(vols[2:] <= deg_in_round[2:])
+    short, _, _ = b.round_stats(cap=1)
+    assert short.tolist() == [int(voff[-1])]
+    b.close()
