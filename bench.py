@@ -235,6 +235,24 @@ def algorithmic_bytes_batch(N, NNZ, sizes, vols, elem):
     return rebase + pass1 + rounds + reduce
 
 
+def algorithmic_bytes_batch_blocks(N, sizes, vols):
+    """Bytes one batched run with one thread block per graph must move to and
+    from device memory (its colors live in shared memory).
+
+    Round k reads the rows of U_k: colidx 4*vol_k and rowptr 8 per vertex, and
+    (k >= 2) the worklist 4|U_k|; it appends U_{k+1} with new colors (8 per
+    vertex) and reads them back once for the color update.  The final colors
+    are written once, 4N.  vol_1 is nnz (every row), |U_1| = N.
+    """
+    total = 4 * N
+    R = len(sizes)
+    for k in range(1, R + 1):
+        u, a = int(sizes[k - 1]), int(vols[k - 1])
+        un = int(sizes[k]) if k < R else 0
+        total += 4 * a + 8 * u + (4 * u if k >= 2 else 0) + 16 * un
+    return total
+
+
 def gathers_rounds(vols):
     """Random neighbour-color reads of the rounds kernel (one per active entry)."""
     return int(sum(int(x) for x in vols[1:]))
@@ -539,13 +557,17 @@ def run_batched(args):
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     stream = torch.cuda.current_stream(dev)
     t = time.time()
-    best, table = gcpkg.autotune_batch(rp_d, ci_d, voff, eoff, reps=2)
+    if args.no_autotune:
+        best, table = {}, []
+    else:
+        best, table = gcpkg.autotune_batch(rp_d, ci_d, voff, eoff, reps=2)
     log(f"autotune {time.time() - t:.1f}s: best {best}")
+    use_graph = args.batch_launch == "graph"
     b = gcpkg.Batch(rp_d, ci_d, voff, eoff, options=best)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.zero_()
-        b.run(graph=True)
+        b.run(graph=use_graph)
     b.status()
     props = torch.cuda.get_device_properties(dev)
     sampler = ClockSampler("GPU-" + str(props.uuid) if getattr(props, "uuid", None) else "0")
@@ -556,7 +578,7 @@ def run_batched(args):
     for a, e in evs:
         flush.zero_()
         a.record(stream)
-        b.run(graph=True)
+        b.run(graph=use_graph)
         e.record(stream)
     torch.cuda.synchronize(dev)
     t1 = time.time()
@@ -566,7 +588,10 @@ def run_batched(args):
     total_s = sum(ms) / 1e3
     sizes, vols, bits = b.round_stats()
     N, NNZ = int(voff[-1]), int(eoff[-1])
-    alg_bytes = algorithmic_bytes_batch(N, NNZ, sizes, vols, bits // 8)
+    if b.mode == 2:
+        alg_bytes = algorithmic_bytes_batch_blocks(N, sizes, vols)
+    else:
+        alg_bytes = algorithmic_bytes_batch(N, NNZ, sizes, vols, bits // 8)
     run_s = total_s / len(evs)
     peak, peak_kind = peaks()
     gathers = gathers_rounds(vols)
@@ -581,7 +606,7 @@ def run_batched(args):
         a.record(stream)
         rp_d.copy_(h_rp, non_blocking=True)
         ci_d.copy_(h_ci, non_blocking=True)
-        b.run(graph=True)
+        b.run(graph=use_graph)
         h_col.copy_(b.colors, non_blocking=True)
         h_nc.copy_(b.ncolors, non_blocking=True)
         e.record(stream)
@@ -594,19 +619,27 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"batch of {len(gs)} graphs, sizes log-uniform in [1,000, 200,000], 2-D grids / "
                                "random geometric (avg degree 8) / R-MAT-G edge factor 8 in turn, seed 4; one "
-                               "persistent launch replayed as a CUDA graph",
+                               "persistent launch " + ("replayed as a CUDA graph" if use_graph else
+                                                        "(plain launches)"),
                    "graphs": len(gs), "N": int(voff[-1]), "nnz": int(eoff[-1]), "m": m_total,
                    "options": best, "max_rounds": max_rounds, "max_colors": max_colors,
                    "workspace_bytes": b.workspace_bytes,
                    "l2": "inputs larger than L2 and L2 flushed (256 MB write) before every step"},
-        "roofline": {"bound": "hbm", "kernel": "whole run (rebase, pass 1, rounds, reduce; one CUDA graph)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("whole run (byte-color and 32-bit passes of batch_local_kernel)" if b.mode == 2
+                                else "whole run (rebase, pass 1, rounds, reduce)"),
+                     "batch_mode": b.mode,
                      "achieved": alg_bytes / run_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": alg_bytes / run_s / 1e9 / peak, "traffic": None,
                      "algorithmic_bytes": alg_bytes, "run_ms": 1e3 * run_s, "color_state_bits": bits,
                      "round_sizes": [int(x) for x in sizes],
-                     "l2_gathers": {"count": gathers, "achieved_G_per_s": gathers / run_s / 1e9,
-                                    "ceiling_G_per_s": L2_GATHER_CEILING,
-                                    "frac": gathers / run_s / 1e9 / L2_GATHER_CEILING}},
+                     **({"shared_memory_gathers": {
+                         "count": int(sum(int(x) for x in vols)),
+                         "achieved_G_per_s": sum(int(x) for x in vols) / run_s / 1e9,
+                         "note": "neighbour colors read from shared memory, all rounds"}} if b.mode == 2 else
+                        {"l2_gathers": {"count": gathers, "achieved_G_per_s": gathers / run_s / 1e9,
+                                        "ceiling_G_per_s": L2_GATHER_CEILING,
+                                        "frac": gathers / run_s / 1e9 / L2_GATHER_CEILING}})},
         "autotune": [{"options": o, "ms": round(t_, 3)} for o, t_ in table],
         "e2e": {"value": m_total / (statistics.mean(e_ms) / 1e3), "unit": "edges/s",
                 "h2d_bytes_per_step": 4 * (rp.size + ci.size), "d2h_bytes_per_step": 4 * (int(voff[-1]) + len(gs)),
@@ -643,6 +676,10 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="time the 4,096-graph batched workload instead (one JSON line)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--batch-launch", choices=["graph", "plain"], default="graph",
+                    help="batched runs as a replayed CUDA graph or as plain launches")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: use the library's default options instead of tuning")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT-B scale (24 is the benchmark; smaller scales are for profiling)")
     ap.add_argument("--measure-l2-ceiling", action="store_true",

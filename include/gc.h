@@ -96,7 +96,17 @@ typedef struct gc_options {
                                   (0 or negative: never, the default: the
                                   last rounds are bound by their longest
                                   task, not by the barrier) */
-    int32_t reserved[6];
+    int32_t batch_mode;        /* gc_batch_create only.  0: choose (default:
+                                  2 when no graph holds more than 2/SMs of
+                                  the batch's vertices + entries, else 1);
+                                  1: all graphs share one persistent grid and
+                                  its rounds (the single-graph kernels on the
+                                  union); 2: one thread block per graph, its
+                                  colors in shared memory (one byte each, up
+                                  to the block's shared memory; larger graphs
+                                  keep them in global memory), graphs taken
+                                  largest first from a queue */
+    int32_t reserved[5];
 } gc_options;
 
 /*
@@ -310,6 +320,11 @@ int gc_batch_destroy(gc_batch* plan);
 /* Bytes of device memory the plan holds; kernels one run launches. */
 size_t gc_batch_workspace_bytes(const gc_batch* plan);
 int64_t gc_batch_launch_count(const gc_batch* plan);
+
+/* gc_batch_mode - how the plan colors its graphs: 1 (one persistent grid over
+ * the union) or 2 (one thread block per graph), as gc_options.batch_mode
+ * describes; GC_ERR_INVALID for NULL. */
+int gc_batch_mode(const gc_batch* plan);
 
 /*
  * Autotuning.  Results never depend on the options (every option set gives

@@ -40,7 +40,7 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
             "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async", "gc_batch_features",
-            "gc_batch_round_stats")
+            "gc_batch_round_stats", "gc_batch_mode")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -84,7 +84,7 @@ class Options(ctypes.Structure):
                 ("loop_mode", ctypes.c_int32), ("color_bits", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),
                 ("narrow_color_limit", ctypes.c_int32), ("tail_volume", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("batch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -134,6 +134,8 @@ def _load():
         lib.gc_batch_features.argtypes = [vp, vp, vp]
         lib.gc_batch_round_stats.argtypes = [vp, vp, vp, i32, vp, vp]
         lib.gc_batch_round_stats.restype = ctypes.c_int
+        lib.gc_batch_mode.argtypes = [vp]
+        lib.gc_batch_mode.restype = ctypes.c_int
         lib.gc_batch_features.restype = ctypes.c_int
         lib.gc_batch_launch_count.argtypes = [vp]
         lib.gc_batch_launch_count.restype = ctypes.c_int64
@@ -623,6 +625,11 @@ class Batch:
         return sizes[:m].copy(), vols[:m].copy(), int(bits.value)
 
     @property
+    def mode(self) -> int:
+        """1: the graphs share one persistent grid; 2: one thread block per graph."""
+        return int(self._lib.gc_batch_mode(self._h))
+
+    @property
     def workspace_bytes(self) -> int:
         return int(self._lib.gc_batch_workspace_bytes(self._h))
 
@@ -646,6 +653,8 @@ class Batch:
 
 TUNE_CANDIDATES = tuple({"small_max_degree": sm, "medium_max_degree": mm, "block_threads": bt}
                         for sm in (8, 16, 32) for mm in (64, 128, 256) for bt in (128, 256))
+# batches: one block per graph, or the grid above shared by all graphs
+BATCH_TUNE_CANDIDATES = ({"batch_mode": 2},) + tuple(dict(c, batch_mode=1) for c in TUNE_CANDIDATES)
 
 
 def _tune_cache_path() -> str:
@@ -730,7 +739,7 @@ def autotune(rowptr, colidx, priority=None, *, candidates=TUNE_CANDIDATES, reps:
 
 
 def autotune_batch(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, priority=None, *,
-                   candidates=TUNE_CANDIDATES, reps: int = 2, cache: bool = True, stream=None):
+                   candidates=BATCH_TUNE_CANDIDATES, reps: int = 2, cache: bool = True, stream=None):
     """Pick the fastest option set for a batch (``gc_batch_tune``); cached per device and
     the batch's degree signature.  Returns (options dict, [(options, ms), ...])."""
     import json
@@ -743,7 +752,7 @@ def autotune_batch(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, priorit
     rp = rowptr_cat.cpu().numpy().astype(np.int64)
     keep = np.ones(max(rp.shape[0] - 1, 0), dtype=bool)
     keep[(voff[1:] + np.arange(G))[:-1]] = False   # the step from one graph's rowptr to the next
-    key = json.dumps(["batch", _device_key(rowptr_cat.device), G, priority is not None,
+    key = json.dumps(["batch", 2, _device_key(rowptr_cat.device), G, priority is not None,
                       _degree_signature(np.diff(rp)[keep] if rp.size > 1 else np.zeros(0))])
     if cache:
         hit = _cache_io(key)

@@ -24,6 +24,7 @@
 #include "gc.h"
 #include "gc_batch.cuh"
 #include "gc_device.cuh"
+#include "gc_local.cuh"
 
 namespace {
 
@@ -351,6 +352,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->color_bits != 0 && o->color_bits != 16 && o->color_bits != 32) return GC_ERR_INVALID;
     if (o->max_rounds < 0 || o->validate < 0 || o->validate > 1) return GC_ERR_INVALID;
     if (o->telemetry != 0 && o->telemetry != 1) return GC_ERR_INVALID;
+    if (o->batch_mode < 0 || o->batch_mode > 2) return GC_ERR_INVALID;
     return GC_OK;
 }
 
@@ -776,6 +778,12 @@ struct gc_batch {
     size_t ws_bytes = 0;
     size_t off_voff = 0, off_eoff = 0, off_rowptr = 0, off_colidx = 0, off_settle = 0, off_flags = 0;
     int64_t launches_per_run = 0;
+    // 1: all graphs share the rounds kernel's grid; 2: one thread block per graph
+    int mode = 1;
+    uint32_t local_smem = 0;  // mode 2: dynamic shared memory per block
+    size_t off_queue = 0, off_order = 0, off_lanes = 0, off_ovf = 0, off_wl0 = 0, off_wl1 = 0, off_gcol8 = 0,
+           off_gcol32 = 0;
+    int32_t* ucolidx = nullptr;  // mode 2: union colidx, allocated when validation or features need it
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -784,18 +792,106 @@ struct gc_batch {
 namespace {
 
 // Rebuild the union colidx from the caller's colidx_cat (local ids -> union ids).
+// The union colidx buffer: part of the plan in mode 1; in mode 2 (which reads
+// the caller's local ids directly) allocated the first time it is needed.
+int union_colidx(gc_batch& b, int32_t** out) {
+    if (b.mode == 1) {
+        *out = (int32_t*)((char*)b.ws + b.off_colidx);
+        return GC_OK;
+    }
+    if (!b.ucolidx) {
+        const cudaError_t e = cudaMalloc(&b.ucolidx, (size_t)std::max<int64_t>(b.NNZ, 1) * 4);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            b.ucolidx = nullptr;
+            return e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA;
+        }
+    }
+    *out = b.ucolidx;
+    return GC_OK;
+}
+
 int batch_rebase(gc_batch& b, cudaStream_t s, int64_t* launches) {
     char* base = (char*)b.ws;
     gc::BatchFlags* fl = (gc::BatchFlags*)(base + b.off_flags);
     GC_CUDA(cudaMemsetAsync(&fl->bad_colidx, 0, sizeof(int), s));
     if (b.NNZ == 0) return GC_OK;
+    int32_t* colidx_g = nullptr;
+    const int rc = union_colidx(b, &colidx_g);
+    if (rc != GC_OK) return rc;
     const int64_t spans = (b.NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b.sms * 8));
     gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(b.colidx_cat, (const int64_t*)(base + b.off_voff),
-                                                 (const int64_t*)(base + b.off_eoff), b.G, b.NNZ,
-                                                 (int32_t*)(base + b.off_colidx), fl);
+                                                 (const int64_t*)(base + b.off_eoff), b.G, b.NNZ, colidx_g, fl);
     GC_CUDA(cudaGetLastError());
     ++*launches;
+    return GC_OK;
+}
+
+// Mode 2: the two launches of the one-block-per-graph kernel (byte colors for
+// every graph, then 32-bit colors for the graphs whose colors outgrew a byte).
+template <bool P>
+int batch_enqueue_local(gc_batch& b, cudaStream_t s) {
+    char* base = (char*)b.ws;
+    gc::LocalParams lp;
+    lp.rowptr_g = (const int32_t*)(base + b.off_rowptr);
+    lp.colidx_cat = b.colidx_cat;
+    lp.prio = b.prio;
+    lp.voff = (const int64_t*)(base + b.off_voff);
+    lp.order = (const int32_t*)(base + b.off_order);
+    lp.lanes_log2 = (const uint8_t*)(base + b.off_lanes);
+    lp.G = b.G;
+    lp.max_rounds = b.o.max_rounds;
+    lp.smem_bytes = b.local_smem;
+    lp.wl0 = (int4*)(base + b.off_wl0);
+    lp.wl1 = (int4*)(base + b.off_wl1);
+    lp.gcol8 = (uint8_t*)(base + b.off_gcol8);
+    lp.gcol32 = (int32_t*)(base + b.off_gcol32);
+    lp.colors_out = b.colors_out;
+    lp.ncolors_out = b.ncolors_out;
+    lp.rounds_out = b.rounds_out;
+    lp.ovf_list = (int32_t*)(base + b.off_ovf);
+    lp.q = (gc::LocalQueue*)(base + b.off_queue);
+    lp.st = (RoundState*)(base + b.L.st);
+    lp.fl = (gc::BatchFlags*)(base + b.off_flags);
+    lp.round_sizes = (int32_t*)(base + b.L.rs);
+    lp.round_vol = (unsigned long long*)(base + b.L.rv);
+    lp.round_cap = (int32_t)b.round_cap;
+    GC_CUDA(cudaMemsetAsync(lp.st, 0, sizeof(RoundState), s));
+    GC_CUDA(cudaMemsetAsync(lp.q, 0, sizeof(gc::LocalQueue), s));
+    GC_CUDA(cudaMemsetAsync(&lp.fl->bad_colidx, 0, sizeof(int), s));
+    GC_CUDA(cudaMemsetAsync(lp.round_sizes, 0, (size_t)b.round_cap * sizeof(int32_t), s));
+    GC_CUDA(cudaMemsetAsync(lp.round_vol, 0, (size_t)b.round_cap * sizeof(unsigned long long), s));
+    gc::batch_local_kernel<uint8_t, P><<<b.sms, gc::kLocalThreads, b.local_smem, s>>>(lp, 0);
+    GC_CUDA(cudaGetLastError());
+    gc::batch_local_kernel<uint32_t, P><<<b.sms, gc::kLocalThreads, b.local_smem, s>>>(lp, 1);
+    GC_CUDA(cudaGetLastError());
+    b.launches_per_run = 2;
+    return GC_OK;
+}
+
+// Dynamic shared memory of the mode-2 kernels (the same for all four forms):
+// all the block may have, less what they declare statically.
+int local_kernels_setup(int device, uint32_t* smem_bytes) {
+    int optin = 0;
+    GC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    const void* kernels[] = {(const void*)gc::batch_local_kernel<uint8_t, false>,
+                             (const void*)gc::batch_local_kernel<uint8_t, true>,
+                             (const void*)gc::batch_local_kernel<uint32_t, false>,
+                             (const void*)gc::batch_local_kernel<uint32_t, true>};
+    size_t stat = 0;
+    for (const void* k : kernels) {
+        cudaFuncAttributes fa;
+        GC_CUDA(cudaFuncGetAttributes(&fa, k));
+        stat = std::max(stat, fa.sharedSizeBytes);
+    }
+    const int dyn = optin - (int)align_up(stat, 1024);
+    if (dyn < 4096) return GC_ERR_CUDA;
+    for (const void* k : kernels) {
+        GC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+        GC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    }
+    *smem_bytes = (uint32_t)dyn;
     return GC_OK;
 }
 
@@ -872,6 +968,7 @@ int batch_enqueue(gc_batch& b, cudaStream_t s) {
     GC_CUDA(cudaGetDevice(&dev));
     if (dev != b.device) return GC_ERR_INVALID;
     if (b.G == 0 || b.N == 0) return GC_OK;
+    if (b.mode == 2) return b.prio ? batch_enqueue_local<true>(b, s) : batch_enqueue_local<false>(b, s);
     return b.bits == 16 ? batch_enqueue_typed<uint16_t>(b, s) : batch_enqueue_typed<int32_t>(b, s);
 }
 
@@ -883,10 +980,9 @@ void batch_free(gc_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->ws) {
-        cudaDeviceSynchronize();
-        cudaFree(b->ws);
-    }
+    if (b->ws || b->ucolidx) cudaDeviceSynchronize();
+    if (b->ws) cudaFree(b->ws);
+    if (b->ucolidx) cudaFree(b->ucolidx);
     cudaSetDevice(cur);
     (void)cudaGetLastError();
     delete b;
@@ -972,10 +1068,67 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
         return fail(GC_ERR_CUDA);
     if (hf.bad_rowptr || b->hs.bad || b->hs.nnz != NNZ) return fail(GC_ERR_BAD_GRAPH);
     b->bits = b->o.color_bits == 32 || b->hs.max_degree + 1 >= 0x8000 ? 32 : 16;
-
-    // the whole plan: head, then the coloring layout, union colidx and settle rounds
     const int32_t max_rounds = b->o.max_rounds > 0 ? b->o.max_rounds : (int32_t)N;
     b->round_cap = std::max<int64_t>(1, std::min<int64_t>(max_rounds, 4096));
+
+    // Mode: one block per graph pays off when no graph is a large share of the
+    // batch's work (vertices + entries): then the graphs keep every SM busy.
+    int64_t max_work = 0;
+    for (int32_t g = 0; g < G; ++g)
+        max_work = std::max<int64_t>(max_work, (voff_h[g + 1] - voff_h[g]) + (eoff_h[g + 1] - eoff_h[g]));
+    b->mode = b->o.batch_mode != 0 ? b->o.batch_mode : (max_work * b->sms <= 2 * (N + NNZ) ? 2 : 1);
+    if (b->mode == 2) {
+        rc = local_kernels_setup(b->device, &b->local_smem);
+        if (rc != GC_OK) return fail(rc);
+        b->bits = 8;
+        off = align_up(head, 256);
+        b->L = Layout{};
+        b->L.st = take(sizeof(RoundState));
+        b->L.rs = take((size_t)b->round_cap * sizeof(int32_t));
+        b->L.rv = take((size_t)b->round_cap * sizeof(unsigned long long));
+        b->off_queue = take(sizeof(gc::LocalQueue));
+        b->off_order = take((size_t)G * 4);
+        b->off_lanes = take((size_t)G);
+        b->off_ovf = take((size_t)G * 4);
+        b->off_wl0 = take((size_t)N * sizeof(int4));
+        b->off_wl1 = take((size_t)N * sizeof(int4));
+        b->off_gcol8 = take((size_t)N);
+        b->off_gcol32 = take((size_t)N * 4);
+        b->ws_bytes = off;
+        b->off_voff = h_voff;
+        b->off_eoff = h_eoff;
+        b->off_rowptr = h_rowptr;
+        b->off_flags = h_flags;
+        // queue order: most work first; lanes per vertex from the average degree
+        std::vector<int32_t> order((size_t)G);
+        std::vector<uint8_t> lanes((size_t)G);
+        for (int32_t g = 0; g < G; ++g) {
+            order[(size_t)g] = g;
+            const int64_t ng = voff_h[g + 1] - voff_h[g], eg = eoff_h[g + 1] - eoff_h[g];
+            const int64_t avg = ng > 0 ? eg / ng : 0;
+            lanes[(size_t)g] = avg <= 6 ? 2 : avg <= 12 ? 3 : avg <= 24 ? 4 : 5;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+            return (voff_h[a + 1] - voff_h[a]) + (eoff_h[a + 1] - eoff_h[a]) >
+                   (voff_h[c + 1] - voff_h[c]) + (eoff_h[c + 1] - eoff_h[c]);
+        });
+        void* ws = nullptr;
+        const cudaError_t e = cudaMalloc(&ws, b->ws_bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA);
+        }
+        b->ws = ws;
+        char* base = (char*)b->ws;
+        if (cudaMemcpyAsync(base, tmp, head, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(base + b->off_order, order.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(base + b->off_lanes, lanes.data(), (size_t)G, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(GC_ERR_CUDA);
+        fail(GC_OK);  // waits for the copies, frees the head copy
+        b->per_sm = 1;
+    } else {
+    if (b->mode != 1) return fail(GC_ERR_INVALID);
     b->L = make_layout(N, NNZ, b->bits == 16 ? 2 : 4, b->hs, b->round_cap);
     off = align_up(head, 256);
     const size_t lay = take(b->L.total);
@@ -1014,17 +1167,21 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
     }
     if (per_sm < 1) return GC_ERR_CUDA;
     b->per_sm = per_sm;
+    }
 
     if (b->o.validate) {
         char* base = (char*)b->ws;
         gc::BatchFlags* fl = (gc::BatchFlags*)(base + b->off_flags);
         const int64_t spans = (NNZ + gc::kRebaseSpan - 1) / gc::kRebaseSpan;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((spans + 7) / 8, (int64_t)b->sms * 8));
+        int32_t* colidx_g = nullptr;
+        rc = union_colidx(*b, &colidx_g);
+        if (rc != GC_OK) return rc;
         GC_CUDA(cudaMemsetAsync(fl, 0, sizeof(gc::BatchFlags), s));
         if (NNZ > 0) {
             gc::batch_colidx_kernel<<<grid, 256, 0, s>>>(colidx_cat, (const int64_t*)(base + b->off_voff),
-                                                         (const int64_t*)(base + b->off_eoff), G, NNZ,
-                                                         (int32_t*)(base + b->off_colidx), fl);
+                                                         (const int64_t*)(base + b->off_eoff), G, NNZ, colidx_g,
+                                                         fl);
             GC_CUDA(cudaGetLastError());
         }
         GC_CUDA(cudaMemcpyAsync(&hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, s));
@@ -1034,8 +1191,7 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
         rc = device_cache(&dcp);
         if (rc != GC_OK) return rc;
         int64_t launches = 0;
-        rc = validate_locked((const int32_t*)(base + b->off_rowptr), (const int32_t*)(base + b->off_colidx),
-                             (int32_t)N, s, *dcp, &launches);
+        rc = validate_locked((const int32_t*)(base + b->off_rowptr), colidx_g, (int32_t)N, s, *dcp, &launches);
         if (rc != GC_OK) return rc;
     }
     GC_CUDA(cudaStreamSynchronize(s));
@@ -1303,8 +1459,9 @@ int gc_batch_features(gc_batch* plan, float* features, void* stream) {
     const int rc = batch_rebase(b, (cudaStream_t)stream, &launches);
     if (rc != GC_OK) return rc;
     char* base = (char*)b.ws;
-    return gc_features((const int32_t*)(base + b.off_rowptr), (const int32_t*)(base + b.off_colidx), (int32_t)b.N,
-                       features, stream);
+    int32_t* colidx_g = nullptr;
+    if (union_colidx(b, &colidx_g) != GC_OK) return GC_ERR_CUDA;
+    return gc_features((const int32_t*)(base + b.off_rowptr), colidx_g, (int32_t)b.N, features, stream);
 }
 
 int gc_batch_launch_graph(gc_batch* plan, void* stream) {
@@ -1425,5 +1582,7 @@ int gc_batch_tune(const int32_t* rowptr_cat, const int32_t* colidx_cat, const in
 size_t gc_batch_workspace_bytes(const gc_batch* plan) { return plan ? plan->ws_bytes : 0; }
 
 int64_t gc_batch_launch_count(const gc_batch* plan) { return plan ? plan->launches_per_run : 0; }
+
+int gc_batch_mode(const gc_batch* plan) { return plan ? plan->mode : GC_ERR_INVALID; }
 
 }  // extern "C"

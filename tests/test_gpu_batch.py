@@ -38,10 +38,21 @@ def _small_mix():
     return gs
 
 
-def _plan(gcpkg, graphs, keys=None, options=None):
+@pytest.fixture(params=[1, 2], ids=["shared-grid", "block-per-graph"])
+def mode(request):
+    """batch_mode: all graphs in one persistent grid (1) or one thread block per graph (2)."""
+    return request.param
+
+
+def _plan(gcpkg, graphs, keys=None, options=None, mode=0):
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in graphs)
     pr = None if keys is None else _dev(np.concatenate(keys).view(np.int32))
-    return gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, pr, options=options), voff
+    opts = dict(options or {})
+    if mode:
+        opts["batch_mode"] = mode
+    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, pr, options=opts)
+    assert not mode or b.mode == mode
+    return b, voff
 
 
 def _check(graphs, b, voff, keys=None, which=None):
@@ -58,23 +69,23 @@ def _check(graphs, b, voff, keys=None, which=None):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_small_mix_bit_exact(gcpkg, graph):
+def test_small_mix_bit_exact(gcpkg, graph, mode):
     gs = _small_mix()
-    b, voff = _plan(gcpkg, gs)
+    b, voff = _plan(gcpkg, gs, mode=mode)
     for _ in range(2):                     # a second run (or graph replay) gives the same
         b.colors.fill_(-1)
         b.run(graph=graph)
         mr, mc = b.status()
         _check(gs, b, voff)
     assert mr == int(b.rounds.max()) and mc == int(b.ncolors.max())
-    assert b.launch_count >= 4
+    assert b.launch_count == (2 if mode == 2 else 5)
     b.close()
 
 
-def test_priority_keys(gcpkg):
+def test_priority_keys(gcpkg, mode):
     gs = _small_mix()
     keys = [(gg.draws(100 + i, 5, g.n) & np.uint64(0xFF)).astype(np.uint32) for i, g in enumerate(gs)]
-    b, voff = _plan(gcpkg, gs, keys)
+    b, voff = _plan(gcpkg, gs, keys, mode=mode)
     b.run(graph=True)
     b.status()
     _check(gs, b, voff, keys)
@@ -84,6 +95,7 @@ def test_priority_keys(gcpkg):
     {"small_max_degree": 8, "medium_max_degree": 64},
     {"small_max_degree": 1, "medium_max_degree": 1, "block_threads": 128},
     {"color_bits": 32},
+    {"batch_mode": 2, "max_rounds": 1000},
 ])
 def test_options_do_not_change_results(gcpkg, options):
     gs = _small_mix()[:30]
@@ -93,24 +105,24 @@ def test_options_do_not_change_results(gcpkg, options):
     _check(gs, b, voff)
 
 
-def test_empty_batches(gcpkg):
+def test_empty_batches(gcpkg, mode):
     b = gcpkg.Batch(_dev(np.zeros(0, np.int32)), _dev(np.zeros(0, np.int32)), np.zeros(1, np.int64),
-                    np.zeros(1, np.int64))
+                    np.zeros(1, np.int64), options={"batch_mode": mode})
     b.run()
     assert b.status() == (0, 0)
     gs = [gg.edgeless(0), gg.edgeless(0)]
-    b, voff = _plan(gcpkg, gs)
+    b, voff = _plan(gcpkg, gs, options={"batch_mode": mode})
     b.run(graph=True)
     assert b.status() == (0, 0)
     assert b.ncolors.cpu().tolist() == [0, 0] and b.rounds.cpu().tolist() == [0, 0]
 
 
-def test_colidx_contents_may_change_between_runs(gcpkg):
+def test_colidx_contents_may_change_between_runs(gcpkg, mode):
     c = gg.cycle(50)                      # every row has 2 entries: any relabelling keeps rowptr
     g1 = [c, gg.star(20, 0)]
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in g1)
     ci_d = _dev(ci)
-    b = gcpkg.Batch(_dev(rp), ci_d, voff, eoff)
+    b = gcpkg.Batch(_dev(rp), ci_d, voff, eoff, options={"batch_mode": mode})
     b.run(graph=True)
     b.status()
     _check(g1, b, voff)
@@ -123,7 +135,7 @@ def test_colidx_contents_may_change_between_runs(gcpkg):
     b.close()
 
 
-def test_rejects_bad_inputs(gcpkg):
+def test_rejects_bad_inputs(gcpkg, mode):
     gs = [gg.path(5), gg.cycle(6)]
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
     down = voff.copy()
@@ -139,10 +151,10 @@ def test_rejects_bad_inputs(gcpkg):
     badc = ci.copy()
     badc[eoff[1]] = 6                                  # id 6 is outside graph 1 (n = 6)
     with pytest.raises(gcpkg.GcError) as e:
-        gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff, options={"validate": 1})
+        gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff, options={"validate": 1, "batch_mode": mode})
     assert e.value.code == gcpkg.GC_ERR_BAD_GRAPH
     # without validation the run replaces the id, stays in bounds and reports it
-    b = gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff)
+    b = gcpkg.Batch(_dev(rp), _dev(badc), voff, eoff, options={"batch_mode": mode})
     b.run()
     with pytest.raises(gcpkg.GcError) as e:
         b.status()
@@ -150,9 +162,12 @@ def test_rejects_bad_inputs(gcpkg):
     with pytest.raises(gcpkg.GcError) as e:           # loop mode needs the host each round
         gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options={"loop_mode": 1})
     assert e.value.code == gcpkg.GC_ERR_INVALID
+    with pytest.raises(gcpkg.GcError) as e:
+        gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options={"batch_mode": 3})
+    assert e.value.code == gcpkg.GC_ERR_INVALID
 
 
-def test_full_size_mix_4096_graphs(gcpkg):
+def test_full_size_mix_4096_graphs(gcpkg, mode):
     """The batched workload: 4,096 graphs, sizes log-uniform in [1,000, 200,000],
     grids / random geometric / R-MAT-G in turn, seed 4, one CUDA-graph launch.
     Sampled graphs against the oracle; every graph against gc_color alone on a
@@ -160,6 +175,10 @@ def test_full_size_mix_4096_graphs(gcpkg):
     gs = gg.batch_mix(4096, 4)
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
     b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff)
+    assert b.mode == 2                        # what the default picks for this workload
+    if mode == 1:
+        b.close()
+        b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options={"batch_mode": 1})
     b.run(graph=True)
     b.run(graph=True)
     b.status()
@@ -200,8 +219,9 @@ def test_autotune_batch(gcpkg, tmp_path, monkeypatch):
     monkeypatch.setenv("GC_TUNE_CACHE", str(tmp_path / "tune.json"))
     gs = _small_mix()
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
-    cands = [{"small_max_degree": 16, "medium_max_degree": 128, "block_threads": 256},
-             {"small_max_degree": 32, "medium_max_degree": 256, "block_threads": 256}]
+    cands = [{"small_max_degree": 16, "medium_max_degree": 128, "block_threads": 256, "batch_mode": 1},
+             {"small_max_degree": 32, "medium_max_degree": 256, "block_threads": 256, "batch_mode": 1},
+             {"batch_mode": 2}]
     best, table = gcpkg.autotune_batch(_dev(rp), _dev(ci), voff, eoff, candidates=cands, reps=2)
     assert best in cands and all(ms > 0 for _, ms in table)
     b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, options=best)
@@ -210,7 +230,7 @@ def test_autotune_batch(gcpkg, tmp_path, monkeypatch):
     _check(gs, b, voff)
 
 
-def test_learned_priority_on_a_batch(gcpkg):
+def test_learned_priority_on_a_batch(gcpkg, mode):
     """Features on the union graph equal each graph's own features, so the learned
     keys of a batch are each graph's learned keys and every graph gets the oracle's
     learned coloring."""
@@ -218,7 +238,7 @@ def test_learned_priority_on_a_batch(gcpkg):
     gs = _small_mix()[:40]
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
     keys = torch.zeros(int(voff[-1]), dtype=torch.int32, device="cuda")
-    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, keys)
+    b = gcpkg.Batch(_dev(rp), _dev(ci), voff, eoff, keys, options={"batch_mode": mode})
     params = gcpkg.load_priority_model()
     b.learned_priority(_dev(params), out=keys)
     f = b.features().cpu().numpy()
@@ -235,16 +255,17 @@ def test_learned_priority_on_a_batch(gcpkg):
     _check(gs, b, voff, keys=want)
 
 
-def test_round_stats(gcpkg):
+def test_round_stats(gcpkg, mode):
     """Per-round telemetry of a batch run: |U_r| over the batch is the sum of
     every graph's own |U_r| (the oracle's), round 1 reads every entry, round 2
-    every row of U_2, and later rounds no more than the rows of U_r."""
+    every row of U_2, and later rounds no more than the rows of U_r (exactly
+    those rows with one block per graph, which reads whole rows)."""
     gs = _small_mix()
-    b, voff = _plan(gcpkg, gs)
+    b, voff = _plan(gcpkg, gs, mode=mode)
     b.run(graph=True)
     mr, _ = b.status()
     sizes, vols, bits = b.round_stats()
-    assert bits in (16, 32) and len(sizes) == len(vols) == mr
+    assert bits == (8 if mode == 2 else 16) and len(sizes) == len(vols) == mr
     want = np.zeros(mr, np.int64)
     deg_in_round = np.zeros(mr, np.int64)
     for g in gs:
@@ -257,6 +278,28 @@ def test_round_stats(gcpkg):
     if mr >= 2:
         assert vols[1] == deg_in_round[1]
     assert np.all(vols[2:] <= deg_in_round[2:])
+    if mode == 2:
+        assert vols[1:].tolist() == deg_in_round[1:].tolist()
     short, _, _ = b.round_stats(cap=1)
     assert short.tolist() == [int(voff[-1])]
     b.close()
+
+
+def test_block_per_graph_wide_colors_and_large_graphs(gcpkg):
+    """One block per graph: a graph whose colors outgrow a byte (K_300 needs 300)
+    is recolored by the 32-bit pass, and a graph too large for shared memory
+    (a 500 x 500 grid, 250,000 vertices) keeps its colors in global memory;
+    both, and the small graphs around them, match the oracle."""
+    gs = [gg.complete(300), gg.path(7), gg.grid2d(500, 500, 3), gg.rgg(3000, 11), gg.complete(30)]
+    b, voff = _plan(gcpkg, gs, mode=2)
+    for graph in (False, True):
+        b.colors.fill_(-1)
+        b.run(graph=graph)
+        mr, mc = b.status()
+        _check(gs, b, voff)
+    assert mc == 300 and mr == 300
+    keys = [(gg.draws(7 + i, 2, g.n) & np.uint64(0xF)).astype(np.uint32) for i, g in enumerate(gs)]
+    b, voff = _plan(gcpkg, gs, keys, mode=2)
+    b.run()
+    b.status()
+    _check(gs, b, voff, keys)
