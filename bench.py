@@ -558,7 +558,7 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
     t = time.time()
     if args.no_autotune:
-        best, table = {}, []
+        best, table = ({"batch_mode": args.batch_mode} if args.batch_mode else {}), []
     else:
         best, table = gcpkg.autotune_batch(rp_d, ci_d, voff, eoff, reps=2)
     log(f"autotune {time.time() - t:.1f}s: best {best}")
@@ -680,6 +680,8 @@ def main():
                     help="batched runs as a replayed CUDA graph or as plain launches")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched: use the library's default options instead of tuning")
+    ap.add_argument("--batch-mode", type=int, choices=[0, 1, 2], default=0,
+                    help="batched, with --no-autotune: gc_options.batch_mode (0: the library chooses)")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT-B scale (24 is the benchmark; smaller scales are for profiling)")
     ap.add_argument("--measure-l2-ceiling", action="store_true",

@@ -106,7 +106,12 @@ typedef struct gc_options {
                                   to the block's shared memory; larger graphs
                                   keep them in global memory), graphs taken
                                   largest first from a queue */
-    int32_t reserved[5];
+    int32_t local_thread_degree; /* batch_mode 2: graphs whose average degree
+                                  is at most this take one thread per vertex
+                                  (default 0 means 32; negative: never); the
+                                  others a group of 4..32 lanes per vertex,
+                                  about half their average degree */
+    int32_t reserved[4];
 } gc_options;
 
 /*

@@ -84,7 +84,8 @@ class Options(ctypes.Structure):
                 ("loop_mode", ctypes.c_int32), ("color_bits", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),
                 ("narrow_color_limit", ctypes.c_int32), ("tail_volume", ctypes.c_int32),
-                ("batch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("batch_mode", ctypes.c_int32), ("local_thread_degree", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None

@@ -1100,13 +1100,16 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
         b->off_rowptr = h_rowptr;
         b->off_flags = h_flags;
         // queue order: most work first; lanes per vertex from the average degree
+        const int64_t tpv = b->o.local_thread_degree == 0 ? 32 : b->o.local_thread_degree;
         std::vector<int32_t> order((size_t)G);
         std::vector<uint8_t> lanes((size_t)G);
         for (int32_t g = 0; g < G; ++g) {
             order[(size_t)g] = g;
             const int64_t ng = voff_h[g + 1] - voff_h[g], eg = eoff_h[g + 1] - eoff_h[g];
-            const int64_t avg = ng > 0 ? eg / ng : 0;
-            lanes[(size_t)g] = avg <= 6 ? 2 : avg <= 12 ? 3 : avg <= 24 ? 4 : 5;
+            const int64_t avg = ng > 0 ? (eg + ng - 1) / ng : 0;
+            int lg = 2;
+            while (lg < 5 && (int64_t(1) << lg) * 2 < avg) ++lg;  // about avg/2 lanes, 4..32
+            lanes[(size_t)g] = (uint8_t)(avg <= tpv ? 0 : lg);
         }
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
             return (voff_h[a + 1] - voff_h[a]) + (eoff_h[a + 1] - eoff_h[a]) >

@@ -19,19 +19,21 @@
 // colors, color count and round count it gets alone.
 //
 // A warp takes 32 worklist entries {v, row start, degree, new color} at a
-// time, one per lane (the next 32 are loaded while these are worked on), and
-// reads their rows with groups of L = 4..32 lanes per vertex (per graph, from
-// its average degree): 32/L vertices side by side, four such steps with
+// time, one per lane (the next 32 are loaded, and L2 is asked for their
+// rows, while these are worked on).  Graphs of average degree up to 32 (by
+// default) take one thread per vertex, eight entries of its row in flight;
+// denser graphs read each row with a group of L = 4..32 lanes (about half
+// the average degree): 32/L vertices side by side, four such steps with
 // their loads issued together, L entries of each row per step (longer rows
-// loop).  A group ORs its findings in one warp reduction -- bits 0..30 mark
-// colors 1..31 among the neighbours, bit 31 a conflict -- and hands them to
-// the vertex's lane, which decides.  When colors 1..31 are all taken, that
-// lane rescans its row in windows of 32 colors.
+// loop), and the group ORs its findings in one warp reduction before handing
+// them to the vertex's lane.  Findings: bits 1..31 mark colors 1..31 among
+// the neighbours, bit 0 a conflict.  When colors 1..31 are all taken, the
+// vertex's lane rescans its row in windows of 32 colors.
 //
 // A color above 255 does not fit a byte: the block gives the graph up and
 // appends it to an overflow list, which a second launch colors with 32-bit
-// colors.  A graph whose colors do not fit shared memory keeps them in
-// global memory (L1-cached) instead, with the same code.
+// colors.  A graph whose colors do not fit shared memory keeps the colors
+// of its first vertices there and the rest in global memory.
 #pragma once
 
 #include "gc_batch.cuh"
@@ -54,7 +56,7 @@ struct LocalParams {
     const uint32_t* __restrict__ prio;      // union-indexed keys, or NULL (index priority)
     const int64_t* __restrict__ voff;       // G + 1 vertex offsets
     const int32_t* __restrict__ order;      // graphs in the order the queue hands them out
-    const uint8_t* __restrict__ lanes_log2; // per graph: log2 of the lanes per vertex (2..5)
+    const uint8_t* __restrict__ lanes_log2; // per graph: log2 of the lanes per vertex (0, or 2..5)
     int32_t G;
     int32_t max_rounds;                     // 0: n_g
     uint32_t smem_bytes;                    // dynamic shared memory per block
@@ -92,28 +94,48 @@ __device__ __forceinline__ bool local_precedes(const uint32_t* __restrict__ prio
 
 // First fit above color 31 for a vertex whose neighbours hold all of 1..31:
 // its lane rescans the row once per window of 32 colors (rare).
-template <typename C>
+template <typename Store>
 __device__ __noinline__ uint32_t local_rescan(const int32_t* __restrict__ colidx, int32_t b, int32_t e,
-                                              const C* col, int32_t n) {
+                                              const Store col, int32_t n) {
     for (uint32_t lo = 32;; lo += 32) {
         uint32_t mm = 0;
         for (int32_t i = b; i < e; ++i) {
-            int32_t w = __ldg(colidx + i);
-            if ((uint32_t)w >= (uint32_t)n) w = 0;
-            const uint32_t c = (uint32_t)col[w];
+            const int32_t w = (int32_t)min((uint32_t)__ldg(colidx + i), (uint32_t)(n - 1));
+            const uint32_t c = (uint32_t)col.get(w);
             if (c - lo < 32u) mm |= 1u << (c - lo);
         }
         if (mm != kFull) return lo + (uint32_t)__ffs(~mm) - 1u;
     }
 }
 
-// Findings of one neighbour w for vertex v (color cv, key pv).
+// Findings word: bit c for a neighbour color c in 1..31, bit 0 for a
+// conflict (a preceding neighbour holds v's color).
+__device__ __forceinline__ uint32_t color_bit(uint32_t c) {
+    uint32_t r;  // shl clamps shifts of 32 and more to 32, giving 0
+    asm("shl.b32 %0, 1, %1;" : "=r"(r) : "r"(c));
+    return r & ~1u;
+}
+
+// Findings of one neighbour w (color c) for vertex v (color cv, key pv).
 template <bool P>
 __device__ __forceinline__ uint32_t local_entry(const uint32_t* __restrict__ prio, int64_t v0, int32_t w, uint32_t c,
                                                 int32_t v, uint32_t cv, uint32_t pv) {
-    uint32_t m = c - 1u < 31u ? 1u << (c - 1u) : 0u;
-    if (c == cv && local_precedes<P>(prio, v0, w, v, pv)) m |= 0x80000000u;
+    uint32_t m = color_bit(c);
+    if (c == cv && local_precedes<P>(prio, v0, w, v, pv)) m |= 1u;
     return m;
+}
+
+// A neighbour id, kept inside the graph (an id outside [0, n) is an input
+// error: it is recorded in `seen` and read as n - 1).
+__device__ __forceinline__ int32_t local_id(int32_t w, int32_t n, uint32_t& seen) {
+    seen = max(seen, (uint32_t)w);
+    return (int32_t)min((uint32_t)w, (uint32_t)(n - 1));
+}
+
+// Ask L2 for the lines of a row that a later step reads.
+__device__ __forceinline__ void local_prefetch_row(const int32_t* row, int32_t d) {
+    for (int32_t o = 0; o < d; o += 32) asm volatile("prefetch.global.L2 [%0];" :: "l"(row + o));
+    if (d > 1) asm volatile("prefetch.global.L2 [%0];" :: "l"(row + d - 1));
 }
 
 // Worklist entry idx of round k: U_1 is every vertex, in order.
@@ -131,28 +153,45 @@ __device__ __forceinline__ int4 local_load_entry(int k, const int4* __restrict__
     return t;
 }
 
-template <typename C, bool P>  // C: color type (byte or 32-bit); P: a priority array is given
-__global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalParams p, int pass) {
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    __shared__ int s_g;
-    __shared__ unsigned s_cnt;
-    __shared__ int s_ovf, s_bad, s_maxc;
-    __shared__ unsigned long long s_vol;
+// Colors of the current graph: in shared memory, or -- for a graph larger
+// than shared memory (SPLIT) -- its first `cap` vertices there and the rest
+// in global memory.
+template <typename C, bool SPLIT>
+struct ColorStore {
+    C* s;          // shared: vertices [0, cap)
+    C* g;          // global, indexed like s (used from cap on)
+    int32_t cap;
+    __device__ __forceinline__ C get(int32_t w) const {
+        if constexpr (SPLIT) return w < cap ? s[w] : g[w];
+        return s[w];
+    }
+    __device__ __forceinline__ void set(int32_t w, C c) const {
+        if constexpr (SPLIT) {
+            if (w < cap) s[w] = c; else g[w] = c;
+        } else {
+            s[w] = c;
+        }
+    }
+};
+
+struct LocalShared {
+    int g;
+    unsigned cnt;
+    int ovf, bad, maxc;
+    unsigned long long vol;
     // per-round telemetry of the current graph (rounds 2..kLocalLog+1), added
     // to the batch's totals once the graph is done, so that a graph handed to
     // the 32-bit pass is not counted twice
-    __shared__ int32_t s_log_cnt[kLocalLog];
-    __shared__ unsigned long long s_log_vol[kLocalLog];
+    int32_t log_cnt[kLocalLog];
+    unsigned long long log_vol[kLocalLog];
+};
+
+// All rounds of graph g, run by the whole block.
+template <typename C, bool P, bool SPLIT>
+__device__ __forceinline__ void local_color_graph(const LocalParams& p, LocalShared& sh, C* s_col, int g,
+                                                  int64_t v0, int32_t n) {
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    for (;;) {
-        if (tid == 0) s_g = (int)atomicAdd(&p.q->next[pass], 1u);
-        __syncthreads();
-        const int qi = s_g;
-        const int limit = pass == 0 ? p.G : (int)__ldcg(&p.q->ovf);
-        if (qi >= limit) break;
-        const int g = pass == 0 ? __ldg(p.order + qi) : __ldcg(p.ovf_list + qi);
-        const int64_t v0 = __ldg(p.voff + g);
-        const int32_t n = (int32_t)(__ldg(p.voff + g + 1) - v0);
+    {
         const int32_t* __restrict__ rp = p.rowptr_g + v0;
         const int lg = __ldg(p.lanes_log2 + g);
         const int L = 1 << lg;
@@ -160,21 +199,21 @@ __global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalPara
         const unsigned gi = lane >> lg;                   // my group
         const int G = 32 >> lg;                           // groups (vertices side by side) per warp
         const unsigned gmask = L == 32 ? kFull : ((1u << L) - 1u) << (gi << lg);
-        C* col;
-        if ((uint64_t)n * sizeof(C) <= p.smem_bytes) {
-            col = reinterpret_cast<C*>(s_dyn);
-        } else if constexpr (sizeof(C) == 1) {
-            col = reinterpret_cast<C*>(p.gcol8 + v0);
+        ColorStore<C, SPLIT> col;
+        col.s = s_col;
+        if constexpr (sizeof(C) == 1) {
+            col.g = reinterpret_cast<C*>(p.gcol8 + v0);
         } else {
-            col = reinterpret_cast<C*>(p.gcol32 + v0);
+            col.g = reinterpret_cast<C*>(p.gcol32 + v0);
         }
+        col.cap = (int32_t)(p.smem_bytes / sizeof(C));
         int4* const wl0 = p.wl0 + v0;
         int4* const wl1 = p.wl1 + v0;
-        for (int32_t i = (int32_t)tid; i < n; i += kLocalThreads) col[i] = (C)1;
+        for (int32_t i = (int32_t)tid; i < n; i += kLocalThreads) col.set(i, (C)1);
         if (tid == 0) {
-            s_ovf = 0;
-            s_bad = 0;
-            s_maxc = 0;
+            sh.ovf = 0;
+            sh.bad = 0;
+            sh.maxc = 0;
         }
         __syncthreads();
         const int32_t maxr = p.max_rounds > 0 ? p.max_rounds : n;
@@ -188,8 +227,8 @@ __global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalPara
             const int4* U = (k & 1) ? wl1 : wl0;  // U_k (k >= 2); U_1 is every vertex
             int4* Nv = (k & 1) ? wl0 : wl1;        // U_{k+1}
             if (tid == 0) {
-                s_cnt = 0u;
-                s_vol = 0ull;
+                sh.cnt = 0u;
+                sh.vol = 0ull;
             }
             __syncthreads();
             // Phase A
@@ -199,12 +238,33 @@ __global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalPara
             for (int32_t base = (int32_t)warp * 32; base < cnt; base += kStride) {
                 const int4 cur = nxt;
                 nxt = local_load_entry(k, U, rp, base + kStride + (int32_t)lane, cnt);
+                local_prefetch_row(p.colidx_cat + nxt.y, nxt.z);  // the next step's row, while this one runs
                 const bool act = base + (int32_t)lane < cnt;
                 const int32_t v = cur.x, b = cur.y, d = cur.z;
-                const uint32_t cv = act ? (uint32_t)col[v] : 0u;
+                const uint32_t cv = act ? (uint32_t)col.get(v) : 0u;
                 uint32_t pv = 0;
                 if constexpr (P) pv = act ? __ldg(p.prio + v0 + v) : 0u;
                 uint32_t mine = 0;  // findings for this lane's vertex
+                uint32_t seen = 0;  // largest neighbour id read (as unsigned)
+                if (lg == 0) {
+                    // one thread per vertex: eight entries of the row in flight
+                    if (act) {
+                        int32_t i = b;
+                        const int32_t e = b + d;
+                        for (; i + 8 <= e; i += 8) {
+                            int32_t x[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) x[u] = local_id(__ldg(p.colidx_cat + i + u), n, seen);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                mine |= local_entry<P>(p.prio, v0, x[u], (uint32_t)col.get(x[u]), v, cv, pv);
+                        }
+                        for (; i < e; ++i) {
+                            const int32_t x = local_id(__ldg(p.colidx_cat + i), n, seen);
+                            mine |= local_entry<P>(p.prio, v0, x, (uint32_t)col.get(x), v, cv, pv);
+                        }
+                    }
+                } else
                 for (int s0 = 0; s0 < L; s0 += 4) {
                     int32_t sv[4], sb[4], sd[4], w[4];
                     uint32_t scv[4], spv[4], m[4];
@@ -218,27 +278,18 @@ __global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalPara
                         spv[u] = P ? __shfl_sync(kFull, pv, src) : 0u;
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) w[u] = (int32_t)j < sd[u] ? __ldg(p.colidx_cat + sb[u] + j) : 0;
+                    for (int u = 0; u < 4; ++u)
+                        w[u] = (int32_t)j < sd[u] ? local_id(__ldg(p.colidx_cat + sb[u] + j), n, seen) : 0;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        m[u] = 0;
-                        if ((int32_t)j < sd[u]) {
-                            if ((uint32_t)w[u] >= (uint32_t)n) {
-                                s_bad = 1;
-                                w[u] = 0;
-                            }
-                            m[u] = local_entry<P>(p.prio, v0, w[u], (uint32_t)col[w[u]], sv[u], scv[u], spv[u]);
-                        }
-                    }
+                    for (int u = 0; u < 4; ++u)
+                        m[u] = (int32_t)j < sd[u]
+                                   ? local_entry<P>(p.prio, v0, w[u], (uint32_t)col.get(w[u]), sv[u], scv[u], spv[u])
+                                   : 0u;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         for (int32_t i = sb[u] + L + (int32_t)j; i < sb[u] + sd[u]; i += L) {
-                            int32_t x = __ldg(p.colidx_cat + i);
-                            if ((uint32_t)x >= (uint32_t)n) {
-                                s_bad = 1;
-                                x = 0;
-                            }
-                            m[u] |= local_entry<P>(p.prio, v0, x, (uint32_t)col[x], sv[u], scv[u], spv[u]);
+                            const int32_t x = local_id(__ldg(p.colidx_cat + i), n, seen);
+                            m[u] |= local_entry<P>(p.prio, v0, x, (uint32_t)col.get(x), sv[u], scv[u], spv[u]);
                         }
                     }
 #pragma unroll
@@ -247,72 +298,95 @@ __global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalPara
                         if ((int)lane / G == s0 + u) mine = r;
                     }
                 }
+                if (seen >= (uint32_t)n) sh.bad = 1;
                 uint32_t newc = 0;
-                if (act && (mine >> 31)) {
-                    const uint32_t avail = ~mine & 0x7fffffffu;
-                    newc = avail ? (uint32_t)__ffs(avail) : local_rescan<C>(p.colidx_cat, b, b + d, col, n);
+                if (act && (mine & 1u)) {
+                    const uint32_t avail = ~mine & ~1u;
+                    newc = avail ? (uint32_t)__ffs(avail) - 1u : local_rescan(p.colidx_cat, b, b + d, col, n);
                 }
                 if (act) vol += (unsigned)d;
                 const bool app = newc != 0u;
                 const unsigned bal = __ballot_sync(kFull, app);
                 unsigned pos = 0;
-                if (lane == 0 && bal) pos = atomicAdd(&s_cnt, (unsigned)__popc(bal));
+                if (lane == 0 && bal) pos = atomicAdd(&sh.cnt, (unsigned)__popc(bal));
                 pos = __shfl_sync(kFull, pos, 0) + (unsigned)__popc(bal & ((1u << lane) - 1u));
                 if (app) {
                     __stcg(Nv + pos, make_int4(v, b, d, (int32_t)newc));
-                    if (newc > LocalColor<C>::kMax) s_ovf = 1;
+                    if (newc > LocalColor<C>::kMax) sh.ovf = 1;
                 }
             }
             vol = __reduce_add_sync(kFull, vol);
-            if (lane == 0 && vol) atomicAdd(&s_vol, (unsigned long long)vol);
+            if (lane == 0 && vol) atomicAdd(&sh.vol, (unsigned long long)vol);
             __syncthreads();
-            const int32_t cnt_next = (int32_t)s_cnt;
+            const int32_t cnt_next = (int32_t)sh.cnt;
             if (tid == 0 && k >= 2) {
                 if (k - 2 < kLocalLog) {
-                    s_log_cnt[k - 2] = cnt;
-                    s_log_vol[k - 2] = s_vol;
+                    sh.log_cnt[k - 2] = cnt;
+                    sh.log_vol[k - 2] = sh.vol;
                 } else if (k - 1 < p.round_cap) {
                     atomicAdd(p.round_sizes + (k - 1), cnt);
-                    atomicAdd(p.round_vol + (k - 1), s_vol);
+                    atomicAdd(p.round_vol + (k - 1), sh.vol);
                 }
             }
-            if (s_ovf) break;
+            if (sh.ovf) break;
             // Phase B: C_{k+1}
             for (int32_t i = (int32_t)tid; i < cnt_next; i += kLocalThreads) {
                 const int4 t = __ldcg(Nv + i);
-                col[t.x] = (C)t.w;
+                col.set(t.x, (C)t.w);
             }
             __syncthreads();
             cnt = cnt_next;
             ++k;
         }
         __syncthreads();
-        if (s_ovf) {
+        if (sh.ovf) {
             if (tid == 0) p.ovf_list[atomicAdd(&p.q->ovf, 1u)] = g;
         } else {
             int mc = 0;
             for (int32_t i = (int32_t)tid; i < n; i += kLocalThreads) {
-                const int c = (int)col[i];
+                const int c = (int)col.get(i);
                 mc = max(mc, c);
                 p.colors_out[v0 + i] = c;
             }
             mc = __reduce_max_sync(kFull, mc);
-            if (lane == 0 && mc) atomicMax(&s_maxc, mc);
+            if (lane == 0 && mc) atomicMax(&sh.maxc, mc);
             for (int r = (int)tid; r < min(k - 2, kLocalLog); r += kLocalThreads)
                 if (r + 1 < p.round_cap) {
-                    atomicAdd(p.round_sizes + r + 1, s_log_cnt[r]);
-                    atomicAdd(p.round_vol + r + 1, s_log_vol[r]);
+                    atomicAdd(p.round_sizes + r + 1, sh.log_cnt[r]);
+                    atomicAdd(p.round_vol + r + 1, sh.log_vol[r]);
                 }
             __syncthreads();
             if (tid == 0) {
-                p.ncolors_out[g] = s_maxc;
+                p.ncolors_out[g] = sh.maxc;
                 p.rounds_out[g] = k - 1;
                 atomicMax(&p.st->rounds, k - 1);
-                atomicMax(&p.st->max_color, s_maxc);
-                if (s_bad) atomicExch(&p.fl->bad_colidx, 1);
+                atomicMax(&p.st->max_color, sh.maxc);
+                if (sh.bad) atomicExch(&p.fl->bad_colidx, 1);
             }
         }
-        __syncthreads();  // shared memory and s_* are reused by the next graph
+    }
+}
+
+template <typename C, bool P>  // C: color type (byte or 32-bit); P: a priority array is given
+__global__ void __launch_bounds__(kLocalThreads, 1) batch_local_kernel(LocalParams p, int pass) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ LocalShared sh;
+    const unsigned tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) sh.g = (int)atomicAdd(&p.q->next[pass], 1u);
+        __syncthreads();
+        const int qi = sh.g;
+        const int limit = pass == 0 ? p.G : (int)__ldcg(&p.q->ovf);
+        if (qi >= limit) break;
+        const int g = pass == 0 ? __ldg(p.order + qi) : __ldcg(p.ovf_list + qi);
+        const int64_t v0 = __ldg(p.voff + g);
+        const int32_t n = (int32_t)(__ldg(p.voff + g + 1) - v0);
+        if ((uint64_t)n * sizeof(C) <= p.smem_bytes) {
+            local_color_graph<C, P, false>(p, sh, reinterpret_cast<C*>(s_dyn), g, v0, n);
+        } else {
+            local_color_graph<C, P, true>(p, sh, reinterpret_cast<C*>(s_dyn), g, v0, n);
+        }
+        __syncthreads();  // shared memory and sh are reused by the next graph
     }
 }
 

@@ -96,6 +96,8 @@ def test_priority_keys(gcpkg, mode):
     {"small_max_degree": 1, "medium_max_degree": 1, "block_threads": 128},
     {"color_bits": 32},
     {"batch_mode": 2, "max_rounds": 1000},
+    {"batch_mode": 2, "local_thread_degree": -1},     # a lane group for every vertex
+    {"batch_mode": 2, "local_thread_degree": 1000},   # one thread for every vertex
 ])
 def test_options_do_not_change_results(gcpkg, options):
     gs = _small_mix()[:30]
