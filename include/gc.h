@@ -111,7 +111,13 @@ typedef struct gc_options {
                                   (default 0 means 32; negative: never); the
                                   others a group of 4..32 lanes per vertex,
                                   about half their average degree */
-    int32_t reserved[4];
+    int32_t local_shared_bytes; /* batch_mode 2: shared memory per block for
+                                  colors, at least 16384 and at most what a
+                                  block can have (0: 167936, which leaves L1
+                                  cache for the rows; a graph with more
+                                  vertices keeps the rest of its colors in
+                                  global memory) */
+    int32_t reserved[3];
 } gc_options;
 
 /*

@@ -85,7 +85,7 @@ class Options(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),
                 ("narrow_color_limit", ctypes.c_int32), ("tail_volume", ctypes.c_int32),
                 ("batch_mode", ctypes.c_int32), ("local_thread_degree", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("local_shared_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 _lib = None
@@ -655,7 +655,8 @@ class Batch:
 TUNE_CANDIDATES = tuple({"small_max_degree": sm, "medium_max_degree": mm, "block_threads": bt}
                         for sm in (8, 16, 32) for mm in (64, 128, 256) for bt in (128, 256))
 # batches: one block per graph, or the grid above shared by all graphs
-BATCH_TUNE_CANDIDATES = ({"batch_mode": 2},) + tuple(dict(c, batch_mode=1) for c in TUNE_CANDIDATES)
+BATCH_TUNE_CANDIDATES = (tuple({"batch_mode": 2, "local_shared_bytes": kb * 1024} for kb in (0, 132, 224))
+                         + tuple(dict(c, batch_mode=1) for c in TUNE_CANDIDATES))
 
 
 def _tune_cache_path() -> str:

@@ -353,6 +353,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->max_rounds < 0 || o->validate < 0 || o->validate > 1) return GC_ERR_INVALID;
     if (o->telemetry != 0 && o->telemetry != 1) return GC_ERR_INVALID;
     if (o->batch_mode < 0 || o->batch_mode > 2) return GC_ERR_INVALID;
+    if (o->local_shared_bytes != 0 && o->local_shared_bytes < 16384) return GC_ERR_INVALID;
     return GC_OK;
 }
 
@@ -887,10 +888,8 @@ int local_kernels_setup(int device, uint32_t* smem_bytes) {
     }
     const int dyn = optin - (int)align_up(stat, 1024);
     if (dyn < 4096) return GC_ERR_CUDA;
-    for (const void* k : kernels) {
+    for (const void* k : kernels)
         GC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
-        GC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    }
     *smem_bytes = (uint32_t)dyn;
     return GC_OK;
 }
@@ -1080,6 +1079,8 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
     if (b->mode == 2) {
         rc = local_kernels_setup(b->device, &b->local_smem);
         if (rc != GC_OK) return fail(rc);
+        b->local_smem = std::min<uint32_t>(
+            b->local_smem, b->o.local_shared_bytes > 0 ? (uint32_t)b->o.local_shared_bytes : 164u * 1024u);
         b->bits = 8;
         off = align_up(head, 256);
         b->L = Layout{};

@@ -305,3 +305,11 @@ def test_block_per_graph_wide_colors_and_large_graphs(gcpkg):
     b.run()
     b.status()
     _check(gs, b, voff, keys)
+    # 16 KB of shared memory: every graph above 16,384 vertices (4,096 with
+    # 32-bit colors) splits its colors between shared and global memory
+    b, voff = _plan(gcpkg, gs, options={"local_shared_bytes": 16384}, mode=2)
+    b.run(graph=True)
+    b.status()
+    _check(gs, b, voff)
+    with pytest.raises(gcpkg.GcError):
+        _plan(gcpkg, gs, options={"local_shared_bytes": 1024}, mode=2)
