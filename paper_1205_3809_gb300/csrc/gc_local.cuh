@@ -21,7 +21,8 @@
 // A warp takes 32 worklist entries {v, row start, degree, new color} at a
 // time, one per lane (the next 32 are loaded, and L2 is asked for their
 // rows, while these are worked on).  Graphs of average degree up to 32 (by
-// default) take one thread per vertex, eight entries of its row in flight;
+// default) take one thread per vertex, eight entries of its row in flight
+// (a row longer than twice the warp's mean is read by the whole warp);
 // denser graphs read each row with a group of L = 4..32 lanes (about half
 // the average degree): 32/L vertices side by side, four such steps with
 // their loads issued together, L entries of each row per step (longer rows
@@ -247,8 +248,37 @@ __device__ __forceinline__ void local_color_graph(const LocalParams& p, LocalSha
                 uint32_t mine = 0;  // findings for this lane's vertex
                 uint32_t seen = 0;  // largest neighbour id read (as unsigned)
                 if (lg == 0) {
-                    // one thread per vertex: eight entries of the row in flight
-                    if (act) {
+                    // one thread per vertex: eight entries of the row in flight.  A row
+                    // longer than twice the warp's mean (and than 16) is read by the
+                    // whole warp instead, so that one long row does not hold 31 idle
+                    // lanes for its length.
+                    const int32_t dsum = (int32_t)__reduce_add_sync(kFull, act ? (unsigned)d : 0u);
+                    const bool longrow = act && d > max(16, (2 * dsum + 31) / 32);
+                    unsigned lb = __ballot_sync(kFull, longrow);
+                    while (lb) {
+                        const int o = __ffs(lb) - 1;
+                        lb &= lb - 1;
+                        const int32_t ob = __shfl_sync(kFull, b, o), od = __shfl_sync(kFull, d, o);
+                        const int32_t ov = __shfl_sync(kFull, v, o);
+                        const uint32_t ocv = __shfl_sync(kFull, cv, o);
+                        const uint32_t opv = P ? __shfl_sync(kFull, pv, o) : 0u;
+                        uint32_t m = 0;
+                        for (int32_t i0 = 0; i0 < od; i0 += 128) {
+                            int32_t x[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int32_t i = i0 + 32 * u + (int32_t)lane;
+                                x[u] = i < od ? local_id(__ldg(p.colidx_cat + ob + i), n, seen) : -1;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                if (x[u] >= 0)
+                                    m |= local_entry<P>(p.prio, v0, x[u], (uint32_t)col.get(x[u]), ov, ocv, opv);
+                        }
+                        m = __reduce_or_sync(kFull, m);
+                        if ((int)lane == o) mine = m;
+                    }
+                    if (act && !longrow) {
                         int32_t i = b;
                         const int32_t e = b + d;
                         for (; i + 8 <= e; i += 8) {
