@@ -317,11 +317,14 @@ int gc_batch_status(gc_batch* plan, void* stream, int32_t* max_rounds, int32_t* 
 int gc_batch_features(gc_batch* plan, float* features, void* stream);
 
 /* gc_batch_round_stats - after a run (waits for `stream`): |U_r| over the whole
- * batch (sizes[r-1], host array of `cap`) and the active adjacency entries
- * round r read (volumes[r-1]; round 1 reads every row) for the first
+ * batch (sizes[r-1], host array of `cap`) and the adjacency entries round r
+ * read (volumes[r-1]; round 1 reads every row; later rounds read the active
+ * entries in batch_mode 1 and whole rows in batch_mode 2) for the first
  * min(rounds, cap, 4096) rounds, and the plan's color-state width in bits
- * (state_bits, 16 or 32).  Any output may be NULL.  Returns that round count,
- * or a gc_status (GC_ERR_INVALID for a NULL plan or cap < 0). */
+ * (state_bits: 16 or 32 in mode 1, 8 in mode 2, whose graphs that need more
+ * are recolored with 32-bit colors; the rounds of such a graph beyond the
+ * 128th are counted twice).  Any output may be NULL.  Returns that round
+ * count, or a gc_status (GC_ERR_INVALID for a NULL plan or cap < 0). */
 int gc_batch_round_stats(gc_batch* plan, int32_t* sizes, int64_t* volumes, int32_t cap, int32_t* state_bits,
                          void* stream);
 

@@ -253,7 +253,7 @@ __device__ __forceinline__ void local_color_graph(const LocalParams& p, LocalSha
                     // whole warp instead, so that one long row does not hold 31 idle
                     // lanes for its length.
                     const int32_t dsum = (int32_t)__reduce_add_sync(kFull, act ? (unsigned)d : 0u);
-                    const bool longrow = act && d > max(16, (2 * dsum + 31) / 32);
+                    const bool longrow = act && (int64_t)d > max((int64_t)16, (2 * (int64_t)dsum + 31) / 32);
                     unsigned lb = __ballot_sync(kFull, longrow);
                     while (lb) {
                         const int o = __ffs(lb) - 1;
