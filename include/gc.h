@@ -331,6 +331,20 @@ int gc_batch_round_stats(gc_batch* plan, int32_t* sizes, int64_t* volumes, int32
 /* gc_batch_destroy - free the plan (waits for the device); NULL is a no-op. */
 int gc_batch_destroy(gc_batch* plan);
 
+/*
+ * gc_color_batched - color a batch in one call: gc_batch_create, one
+ * gc_batch_run and gc_batch_status on `stream`, then gc_batch_destroy.
+ * Arguments as for gc_batch_create (offsets on the host, everything else on
+ * the device, opt may be NULL).  Returns when the results are in colors_out,
+ * ncolors_out and rounds_out, with the status of the run (GC_ERR_BAD_GRAPH
+ * for an id outside its graph, GC_ERR_MAX_ROUNDS, ...).  For repeated runs on
+ * the same batch, keep a plan instead: planning allocates and scans.
+ */
+int gc_color_batched(const int64_t* vertex_offsets, const int64_t* edge_offsets, int32_t num_graphs,
+                     const int32_t* rowptr_cat, const int32_t* colidx_cat, const uint32_t* priority,
+                     int32_t* colors_out, int32_t* ncolors_out, int32_t* rounds_out, void* stream,
+                     const gc_options* opt);
+
 /* Bytes of device memory the plan holds; kernels one run launches. */
 size_t gc_batch_workspace_bytes(const gc_batch* plan);
 int64_t gc_batch_launch_count(const gc_batch* plan);

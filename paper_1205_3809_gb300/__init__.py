@@ -40,7 +40,7 @@ EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_s
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
             "gc_batch_launch_count", "gc_tune", "gc_batch_tune", "gc_color_async", "gc_batch_features",
-            "gc_batch_round_stats", "gc_batch_mode")
+            "gc_batch_round_stats", "gc_batch_mode", "gc_color_batched")
 
 
 class GcLibraryMissing(RuntimeError):
@@ -137,6 +137,8 @@ def _load():
         lib.gc_batch_round_stats.restype = ctypes.c_int
         lib.gc_batch_mode.argtypes = [vp]
         lib.gc_batch_mode.restype = ctypes.c_int
+        lib.gc_color_batched.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Options)]
+        lib.gc_color_batched.restype = ctypes.c_int
         lib.gc_batch_features.restype = ctypes.c_int
         lib.gc_batch_launch_count.argtypes = [vp]
         lib.gc_batch_launch_count.restype = ctypes.c_int64
@@ -521,6 +523,37 @@ def pack_batch(graphs):
     rowptr_cat = np.concatenate(rps) if rps else np.zeros(0, np.int32)
     colidx_cat = np.concatenate(cis) if cis else np.zeros(0, np.int32)
     return rowptr_cat, colidx_cat, np.asarray(nv, np.int64), np.asarray(ne, np.int64)
+
+
+def color_batched(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, priority=None, *, options=None,
+                  stream=None):
+    """Color a batch in one call (``gc_color_batched``): plan, one run, status, free.
+    Same arguments as ``Batch``; returns (colors, ncolors, rounds) as CUDA tensors."""
+    import torch
+    lib = _load()
+    voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+    eoff = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+    G = int(voff.shape[0]) - 1
+    if G < 0 or eoff.shape[0] != G + 1:
+        raise ValueError("vertex_offsets and edge_offsets must both have G+1 entries")
+    N, NNZ = int(voff[-1]), int(eoff[-1])
+    dev = rowptr_cat.device
+    colors = torch.empty(N, dtype=torch.int32, device=dev)
+    ncolors = torch.empty(G, dtype=torch.int32, device=dev)
+    rounds = torch.empty(G, dtype=torch.int32, device=dev)
+    pr = None if priority is None else _dev_ptr(priority, priority.dtype, "priority", N)
+    opt = _options(options)
+    with torch.cuda.device(dev):
+        rc = lib.gc_color_batched(ctypes.c_void_p(voff.ctypes.data), ctypes.c_void_p(eoff.ctypes.data), G,
+                                  _dev_ptr(rowptr_cat, torch.int32, "rowptr_cat", N + G),
+                                  _dev_ptr(colidx_cat, torch.int32, "colidx_cat", NNZ), pr,
+                                  _dev_ptr(colors, torch.int32, "colors", N),
+                                  _dev_ptr(ncolors, torch.int32, "ncolors", G),
+                                  _dev_ptr(rounds, torch.int32, "rounds", G), _stream_handle(stream, dev),
+                                  ctypes.byref(opt) if opt is not None else None)
+    if rc != GC_OK:
+        raise GcError(rc, "gc_color_batched", lib.gc_last_cuda_error())
+    return colors, ncolors, rounds
 
 
 class Batch:

@@ -1505,6 +1505,20 @@ int gc_batch_destroy(gc_batch* plan) {
     return GC_OK;
 }
 
+int gc_color_batched(const int64_t* vertex_offsets, const int64_t* edge_offsets, int32_t num_graphs,
+                     const int32_t* rowptr_cat, const int32_t* colidx_cat, const uint32_t* priority,
+                     int32_t* colors_out, int32_t* ncolors_out, int32_t* rounds_out, void* stream,
+                     const gc_options* opt) {
+    gc_batch* plan = nullptr;
+    int rc = gc_batch_create(rowptr_cat, colidx_cat, vertex_offsets, edge_offsets, num_graphs, priority, colors_out,
+                             ncolors_out, rounds_out, opt, stream, &plan);
+    if (rc != GC_OK) return rc;
+    rc = gc_batch_run(plan, stream);
+    if (rc == GC_OK) rc = gc_batch_status(plan, stream, nullptr, nullptr);
+    gc_batch_destroy(plan);
+    return rc;
+}
+
 namespace {
 // Median of the timed runs of one candidate.
 float median_ms(std::vector<float>& v) {

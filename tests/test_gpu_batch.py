@@ -313,3 +313,20 @@ def test_block_per_graph_wide_colors_and_large_graphs(gcpkg):
     _check(gs, b, voff)
     with pytest.raises(gcpkg.GcError):
         _plan(gcpkg, gs, options={"local_shared_bytes": 1024}, mode=2)
+
+
+def test_color_batched_one_call(gcpkg, mode):
+    """gc_color_batched (plan, run, status, free in one call) gives what a plan gives."""
+    gs = _small_mix()[:25]
+    rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+    colors, nc, rd = gcpkg.color_batched(_dev(rp), _dev(ci), voff, eoff, options={"batch_mode": mode})
+    b, _ = _plan(gcpkg, gs, mode=mode)
+    b.run()
+    b.status()
+    assert torch.equal(colors, b.colors) and torch.equal(nc, b.ncolors) and torch.equal(rd, b.rounds)
+    _check(gs, b, voff)
+    badc = ci.copy()
+    badc[eoff[1]] = 10 ** 6
+    with pytest.raises(gcpkg.GcError) as e:
+        gcpkg.color_batched(_dev(rp), _dev(badc), voff, eoff, options={"batch_mode": mode})
+    assert e.value.code == gcpkg.GC_ERR_BAD_GRAPH
