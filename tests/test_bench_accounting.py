@@ -1,0 +1,52 @@
+"""Host-side accounting of bench.py (no GPU): algorithmic bytes and gathers per
+run, and the code hash that ties committed ncu counters to the kernel source."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_rounds_bytes_by_hand():
+    # rounds 1..3: |U| = 10, 6, 2; entries read 40, 24, 5; 2-byte color state
+    sizes, vols, elem = [10, 6, 2], [40, 24, 5], 2
+    # k = 2: reads 4*24 + 2*24 + 16*6 + 2*6 (no static masks yet); writes 4*5 + 16*2 + 32*2 + 2*6 + 4*4
+    k2 = (96 + 48 + 96 + 12) + (20 + 32 + 64 + 12 + 16)
+    # k = 3 (last): reads 4*5 + 2*5 + 16*2 + 2*2 + 32*2; writes 2*2 + 4*2 (both settle)
+    k3 = (20 + 10 + 32 + 4 + 64) + (4 + 8)
+    assert bench.algorithmic_bytes_rounds(sizes, vols, elem) == k2 + k3
+
+
+def test_block_per_graph_bytes_by_hand():
+    # N = 10 vertices; rounds 1..3: |U| = 10, 6, 2; rows read 40, 24, 5
+    sizes, vols = [10, 6, 2], [40, 24, 5]
+    r1 = 4 * 40 + 8 * 10 + 16 * 6
+    r2 = 4 * 24 + 8 * 6 + 4 * 6 + 16 * 2
+    r3 = 4 * 5 + 8 * 2 + 4 * 2
+    assert bench.algorithmic_bytes_batch_blocks(10, sizes, vols) == 4 * 10 + r1 + r2 + r3
+
+
+def test_shared_grid_batch_bytes_by_hand():
+    N, NNZ, sizes, vols, elem = 10, 40, [10, 6, 2], [40, 24, 5], 2
+    u2 = 6
+    want = (8 * NNZ + (4 * (N + 1) + 4 * NNZ + 2 * elem * N + 8 * (N - u2) + 16 * u2)
+            + bench.algorithmic_bytes_rounds(sizes, vols, elem) + 4 * u2 + 8 * N)
+    assert bench.algorithmic_bytes_batch(N, NNZ, sizes, vols, elem) == want
+
+
+def test_gathers_skip_round_one():
+    assert bench.gathers_rounds([40, 24, 5]) == 29
+    assert bench.gathers_rounds([7]) == 0
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    a = tmp_path / "a.cuh"
+    a.write_text("// header\nint f(int x) {  // note\n  return x + 1;\n}\n\n/* block\n comment */\n")
+    b = tmp_path / "b.cuh"
+    b.write_text("int f(int x) {\n  return x + 1;\n}\n")
+    c = tmp_path / "c.cuh"
+    c.write_text("int f(int x) {\n  return x + 2;\n}\n")
+    assert bench.kernel_code_hash(str(a)) == bench.kernel_code_hash(str(b))
+    assert bench.kernel_code_hash(str(b)) != bench.kernel_code_hash(str(c))
