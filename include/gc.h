@@ -251,12 +251,16 @@ int gc_color_async(const int32_t* rowptr, const int32_t* colidx, int32_t n, cons
 /*
  * Batched coloring: many independent graphs in one persistent launch.
  *
- * Algorithm 2 (Sec. 3.2) in synchronous rounds on each graph of a batch, all
- * graphs advancing together in one cooperative launch.  The batch is colored
- * as the disjoint union of its graphs (vertex i of graph g = union vertex
- * voff[g] + i, which keeps the order of indices inside every graph), so each
- * graph gets exactly the colors, color count and round count that gc_color
- * gives it alone.
+ * Algorithm 2 (Sec. 3.2) in synchronous rounds on each graph of a batch, so
+ * that each graph gets exactly the colors, color count and round count that
+ * gc_color gives it alone, in one of two ways (gc_options.batch_mode):
+ *   2: persistent thread blocks, one per SM, each taking whole graphs from a
+ *      queue (largest first) and running all of a graph's rounds with its
+ *      colors in shared memory (the default when no graph is a large share
+ *      of the batch);
+ *   1: all graphs advancing together in one cooperative launch over their
+ *      disjoint union (vertex i of graph g = union vertex voff[g] + i, which
+ *      keeps the order of indices inside every graph).
  *
  * Input layout (device arrays owned by the caller), for G graphs:
  *   vertex_offsets[G+1], edge_offsets[G+1] (HOST int64 arrays): graph g has
@@ -274,8 +278,9 @@ int gc_color_async(const int32_t* rowptr, const int32_t* colidx, int32_t n, cons
  *
  * gc_batch_create plans the batch: it checks the offsets and every graph's
  * rowptr, builds the union rowptr, scans degrees, allocates the plan's
- * workspace (roughly 80 bytes per vertex plus 12 per adjacency entry) and, with
- * opt->validate, checks ids, self loops and symmetry.  It synchronises
+ * workspace (mode 1: roughly 80 bytes per vertex plus 12 per adjacency entry;
+ * mode 2: roughly 45 bytes per vertex) and, with opt->validate, checks ids,
+ * self loops and symmetry.  It synchronises
  * `stream`.  The plan keeps the array pointers: later runs read the caller's
  * colidx_cat and priority and write the outputs, so their contents may change
  * between runs, but rowptr_cat is read only here (the degrees are fixed).
