@@ -46,3 +46,16 @@ def test_no_cpu_fallback_in_binding():
     src = open(os.path.join(ROOT, "paper_1205_3809_gb300", "__init__.py")).read()
     assert "oracle" not in src.replace("oracle.", "")
     assert "import oracle" not in src
+
+
+def test_options_struct_mirrors_header():
+    """Options (ctypes) has the fields of gc_options, in the header's order, all int32."""
+    import paper_1205_3809_gb300 as m
+    text = open(os.path.join(ROOT, "include", "gc.h")).read()
+    body = text[text.index("typedef struct gc_options {"):text.index("} gc_options;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int32_t\s+(\w+)(?:\[(\d+)\])?\s*;", body)
+    names = [f for f, _ in fields]
+    assert names == [f for f, _ in m.Options._fields_]
+    width = sum(int(n) if n else 1 for _, n in fields)
+    assert ctypes.sizeof(m.Options) == 4 * width
