@@ -162,6 +162,23 @@ def oracle_rate(scale, runs=1):
     return g, r, times
 
 
+def paper_async_openmp(scale):
+    """The paper's own multicore method (asynchronous Algorithm 2, OpenMP, all host
+    cores) on the CPU-baseline graph, in a child process with a time limit;
+    checked for validity only.  Never fails the bench: a problem is reported."""
+    try:
+        r = subprocess.run([sys.executable, "-m", "oracle.async_omp", "--scale", str(scale), "--seed", "3"],
+                           cwd=ROOT, capture_output=True, text=True, timeout=300)
+        if r.returncode != 0:
+            return {"unavailable": f"exit {r.returncode}: {r.stderr.strip()[-200:]}"}
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out["note"] = ("Algorithm 2 as the paper runs it on multicore CPUs: asynchronous Phase 1, "
+                       "schedule-dependent, validity-checked")
+        return out
+    except (subprocess.TimeoutExpired, ValueError, IndexError, OSError) as e:
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -421,7 +438,8 @@ def run_ours(args):
                "host": {"cpus": os.cpu_count(), "machine": platform.machine(), "model": cpu_model()},
                "greedy_serial": {"value": cg.m / greedy_s, "unit": "edges/s", "seconds": round(greedy_s, 3),
                                  "ncolors": greedy_colors,
-                                 "note": "Algorithm 1 in index order, one core (the sequential baseline)"}}
+                                 "note": "Algorithm 1 in index order, one core (the sequential baseline)"},
+               "paper_async_openmp": paper_async_openmp(CPU_BASELINE_SCALE)}
 
     if rank == 0:
         line = {

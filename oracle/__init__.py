@@ -22,17 +22,23 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SRC_LEARNED = os.path.join(_HERE, "learned.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_SRC_ASYNC = os.path.join(_HERE, "async_omp.c")
+_LIB_ASYNC = os.path.join(_HERE, "libasync_omp.so")
 
 ORC_OK = 0
 ORC_ERR_MAX_ROUNDS = -4
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (single-threaded, -O2, no FMA contraction)."""
+    """Compile liboracle.so (single-threaded, -O2, no FMA contraction) and, apart
+    from it, libasync_omp.so (the paper's OpenMP form, a timed baseline only)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_LEARNED))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-Wall",
                "-o", _LIB, _SRC, _SRC_LEARNED, "-lm"]
+        subprocess.run(cmd, check=True)
+    if force or not os.path.exists(_LIB_ASYNC) or os.path.getmtime(_LIB_ASYNC) < os.path.getmtime(_SRC_ASYNC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall", "-o", _LIB_ASYNC, _SRC_ASYNC]
         subprocess.run(cmd, check=True)
     return _LIB
 
