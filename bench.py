@@ -162,6 +162,22 @@ def oracle_rate(scale, runs=1):
     return g, r, times
 
 
+def batch_cpu_baseline(graphs, stride=64):
+    """The single-threaded oracle on every `stride`-th graph of a batch (a bounded
+    sample of the same workload): edges/s, with what the sample was."""
+    import oracle
+    oracle.build()
+    sample = graphs[::stride]
+    m = sum(g.m for g in sample)
+    t = time.perf_counter()
+    for g in sample:
+        oracle.iterative(g.rowptr, g.colidx)
+    s = time.perf_counter() - t
+    return {"value": m / s if s > 0 else None, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"every {stride}th graph of the batch: {len(sample)} graphs, {m} edges, {s:.1f} s",
+            "host": {"cpus": os.cpu_count(), "machine": platform.machine(), "model": cpu_model()}}
+
+
 def paper_async_openmp(scale):
     """The paper's own multicore method (asynchronous Algorithm 2, OpenMP, all host
     cores) on the CPU-baseline graph, in a child process with a time limit;
@@ -664,6 +680,7 @@ def run_batched(args):
                 "ms_per_step": statistics.mean(e_ms)},
         "gpu_launches": b.launch_count * args.steps,
         "clocks": clocks,
+        "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(gs),
     }
     print(json.dumps(line), flush=True)
     b.close()

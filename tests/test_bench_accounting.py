@@ -50,3 +50,11 @@ def test_code_hash_ignores_comments_only(tmp_path):
     c.write_text("int f(int x) {\n  return x + 2;\n}\n")
     assert bench.kernel_code_hash(str(a)) == bench.kernel_code_hash(str(b))
     assert bench.kernel_code_hash(str(b)) != bench.kernel_code_hash(str(c))
+
+
+def test_batch_cpu_baseline_on_a_small_sample():
+    import graphgen as gg
+    gs = gg.batch_mix(8, 4, n_min=100, n_max=400)
+    r = bench.batch_cpu_baseline(gs, stride=4)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+    assert r["sample"].startswith("every 4th graph of the batch: 2 graphs")
