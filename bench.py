@@ -250,6 +250,34 @@ def algorithmic_bytes_rounds(sizes, vols, elem):
     return total
 
 
+def fixed_bytes_rounds(sizes, degree_vols):
+    """Bytes of rounds k >= 2 under the fixed full-row accounting, the same for
+    every implementation of the method: per round k over W = U_k, the worklist
+    4|W|, the rowptr pair 8|W|, colidx and the neighbours' colors 8 vol(W)
+    (vol(W) = sum of deg(v) over W, whole rows), the own color 4|W| and the
+    appends of the next round 8|U_{k+1}|."""
+    total = 0
+    R = len(sizes)
+    for k in range(2, R + 1):
+        u, un = int(sizes[k - 1]), (int(sizes[k]) if k < R else 0)
+        total += 16 * u + 8 * int(degree_vols[k - 1]) + 8 * un
+    return total
+
+
+def stored_degree_volumes(n, nnz, sizes):
+    """Per-round degree volumes of this workload as the oracle computed them
+    (tests/golden/fullsize.json, written by tests/golden/make_fullsize.py), when
+    the run's |U_k| are the stored ones; else None."""
+    path = os.path.join(ROOT, "tests", "golden", "fullsize.json")
+    if not os.path.exists(path):
+        return None
+    for entry in json.load(open(path)).values():
+        if (entry.get("n") == n and entry.get("nnz") == nnz and entry.get("round_sizes") == [int(x) for x in sizes]
+                and "round_degree_volumes" in entry):
+            return entry["round_degree_volumes"]
+    return None
+
+
 def algorithmic_bytes_batch(N, NNZ, sizes, vols, elem):
     """Bytes one batched run must move, all of its kernels together.
 
@@ -406,7 +434,9 @@ def run_ours(args):
 
     sizes, vols = gcpkg.last_round_stats()
     elem = 2  # 16-bit color state (the library restarts with 32 bits only past 32767 colors)
-    alg_bytes = algorithmic_bytes_rounds(sizes, vols, elem)
+    active_bytes = algorithmic_bytes_rounds(sizes, vols, elem)
+    degree_vols = stored_degree_volumes(g.n, g.nnz, sizes)
+    alg_bytes = fixed_bytes_rounds(sizes, degree_vols) if degree_vols else active_bytes
     kms = statistics.mean(kernel_ms)
     achieved = alg_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
@@ -476,6 +506,12 @@ def run_ours(args):
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes": alg_bytes, "kernel_ms": kms,
+                         "accounting": ("whole rows: fixed per-round bytes of the method (worklist, rowptr, "
+                                        "colidx and neighbour colors of every row of U_k, own color, appends)"
+                                        if degree_vols else "active entries (this implementation's reads)"),
+                         "active_entries": {"algorithmic_bytes": active_bytes,
+                                            "achieved": active_bytes / (kms / 1e3) / 1e9,
+                                            "frac": active_bytes / (kms / 1e3) / 1e9 / peak},
                          "l2_gathers": {"count": gathers, "achieved_G_per_s": gather_rate,
                                         "ceiling_G_per_s": L2_GATHER_CEILING,
                                         "frac": gather_rate / L2_GATHER_CEILING},

@@ -1,7 +1,9 @@
 """Write tests/golden/fullsize.json: the oracle's result on the full-size
 synthetic workloads (index priority, and the shipped learned priority with
 keys the oracle computes itself), stored as a SHA-256 of the int32 colors plus
-ncolors, rounds and |U_r| of every round.  Calls only graphgen/ and oracle/.
+ncolors, rounds, |U_r| of every round and the degree volume of every round
+(the sum of deg(v) over U_r, which the bench's fixed byte accounting needs).
+Calls only graphgen/ and oracle/.
 
     python tests/golden/make_fullsize.py [name ...]
 """
@@ -43,6 +45,12 @@ def learned_keys(g):
     return L.learned_keys(g.rowptr, g.colidx, params)
 
 
+def degree_volumes(g, r):
+    """vol_k = sum of deg(v) over U_k, k = 1..rounds (v is in U_k iff it settled in round k or later)."""
+    by_round = np.bincount(r.settle_round, weights=g.degrees.astype(np.float64), minlength=r.rounds + 1)
+    return [int(x) for x in np.cumsum(by_round[::-1])[::-1][1:r.rounds + 1]]
+
+
 def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).astype("<i4").tobytes()).hexdigest()
 
@@ -61,6 +69,7 @@ def main(names):
                                            + g.colidx.astype("<i4").tobytes()).hexdigest(),
             "colors_sha256": sha(r.colors), "ncolors": r.ncolors, "rounds": r.rounds,
             "round_sizes": r.round_sizes.tolist(),
+            "round_degree_volumes": degree_volumes(g, r),
             "oracle_seconds": round(time.time() - t, 1),
         }
         print(name, out[name]["ncolors"], out[name]["rounds"], out[name]["oracle_seconds"], flush=True)

@@ -58,3 +58,22 @@ def test_batch_cpu_baseline_on_a_small_sample():
     r = bench.batch_cpu_baseline(gs, stride=4)
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
     assert r["sample"].startswith("every 4th graph of the batch: 2 graphs")
+
+
+def test_fixed_full_row_bytes_by_hand():
+    # rounds 1..3: |U| = 10, 6, 2; degree volumes (whole rows) 40, 30, 9
+    sizes, dv = [10, 6, 2], [40, 30, 9]
+    k2 = 16 * 6 + 8 * 30 + 8 * 2
+    k3 = 16 * 2 + 8 * 9
+    assert bench.fixed_bytes_rounds(sizes, dv) == k2 + k3
+
+
+def test_stored_degree_volumes_match_only_the_stored_run():
+    import json
+    entry = json.load(open(os.path.join(ROOT, "tests", "golden", "fullsize.json")))["rmat_b_s24_seed3"]
+    got = bench.stored_degree_volumes(entry["n"], entry["nnz"], entry["round_sizes"])
+    assert got == entry["round_degree_volumes"] and got[0] == entry["nnz"]
+    assert all(a >= b for a, b in zip(got, got[1:]))            # U_k shrinks round by round
+    assert bench.stored_degree_volumes(entry["n"], entry["nnz"], entry["round_sizes"][:-1]) is None
+    # whole rows read at least what the active lists read: 23.8 nnz after round 1 on this graph
+    assert abs(sum(got[1:]) / entry["nnz"] - 23.8) < 0.05
