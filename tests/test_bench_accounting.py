@@ -77,3 +77,9 @@ def test_stored_degree_volumes_match_only_the_stored_run():
     assert bench.stored_degree_volumes(entry["n"], entry["nnz"], entry["round_sizes"][:-1]) is None
     # whole rows read at least what the active lists read: 23.8 nnz after round 1 on this graph
     assert abs(sum(got[1:]) / entry["nnz"] - 23.8) < 0.05
+
+
+def test_fixed_bytes_of_a_whole_call_by_hand():
+    n, nnz, sizes, dv = 10, 40, [10, 6, 2], [40, 30, 9]
+    want = 4 * 11 + 4 * 40 + 4 * 10 + 8 * 6 + bench.fixed_bytes_rounds(sizes, dv) + 8 * 10
+    assert bench.fixed_bytes_call(n, nnz, sizes, dv) == want
