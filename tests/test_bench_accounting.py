@@ -83,3 +83,16 @@ def test_fixed_bytes_of_a_whole_call_by_hand():
     n, nnz, sizes, dv = 10, 40, [10, 6, 2], [40, 30, 9]
     want = 4 * 11 + 4 * 40 + 4 * 10 + 8 * 6 + bench.fixed_bytes_rounds(sizes, dv) + 8 * 10
     assert bench.fixed_bytes_call(n, nnz, sizes, dv) == want
+
+
+def test_golden_degree_volumes_follow_their_definition():
+    """make_fullsize.degree_volumes (suffix sums of degrees by settle round) equals
+    the definition vol_k = sum of deg(v) over U_k = {v : settle(v) >= k}."""
+    import graphgen as gg
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_fullsize
+    for g in (gg.rmat(11, 8, gg.RMAT_B, 3), gg.complete(12), gg.edgeless(3), gg.path(9)):
+        r = oracle.iterative(g.rowptr, g.colidx)
+        want = [int(g.degrees[r.settle_round >= k].sum()) for k in range(1, r.rounds + 1)]
+        assert make_fullsize.degree_volumes(g, r) == want
