@@ -62,11 +62,11 @@ typedef struct gc_options {
                                   most this many entries go 32 to a warp task
                                   (1..32, default 32) */
     int32_t medium_max_degree; /* active lists up to this length (and above
-                                  the small limit) go 4 to a warp task (1 when
-                                  that would leave warps idle); longer lists
-                                  are split into chunks of 1024 entries, one
-                                  warp each (small_max_degree..256, default
-                                  256) */
+                                  the small limit) go 8 to a warp task (1 when
+                                  that would leave warps idle), each list read
+                                  by the whole warp in turn; longer lists are
+                                  split into chunks of 1024 entries, one warp
+                                  each (small_max_degree..256, default 256) */
     int32_t max_rounds;        /* stop with GC_ERR_MAX_ROUNDS after this many
                                   rounds (default n; rounds <= n always holds,
                                   since the first vertex of U in precedence
@@ -117,7 +117,17 @@ typedef struct gc_options {
                                   cache for the rows; a graph with more
                                   vertices keeps the rest of its colors in
                                   global memory) */
-    int32_t reserved[3];
+    int32_t barrier_poll_limit; /* testing, loop_mode 0: the grid barrier
+                                  between rounds gives up after this many
+                                  polls (0: after 2^26 polls or 4 s), sets
+                                  GC_ERR_TIMEOUT and every block leaves; the
+                                  next call starts from a clean state */
+    int32_t workspace_limit_mb; /* testing: a call that would have to grow
+                                  the device workspace beyond this many MiB
+                                  fails with GC_ERR_OOM without allocating
+                                  (as if cudaMalloc had refused), keeping the
+                                  workspace it already has (0: no limit) */
+    int32_t reserved[1];
 } gc_options;
 
 /*
@@ -185,6 +195,20 @@ int gc_last_round_stats(int32_t* sizes, int64_t* volumes, int32_t cap);
  * Returns the number of values written (<= cap, at most 4) or GC_ERR_INVALID.
  */
 int gc_last_phase_ms(float* ms, int32_t cap);
+
+/*
+ * gc_last_round_ns - how long each round took in the last call made with
+ * opt->telemetry = 1 and loop_mode 0 (one persistent launch): ns[0] = 0
+ * (round 1 and its conflict test run before that launch; gc_last_phase_ms
+ * times them), ns[k-1] = nanoseconds from the start of the pass that runs
+ * round k's conflict test (and round k+1's tentative coloring) to the start
+ * of the next, for k = 2..min(rounds, cap, 4096 or that call's
+ * round_sizes_cap), read from the device's %globaltimer by one thread after
+ * each grid barrier (its resolution is the device's, typically 32 ns to
+ * 1 us).  Returns the number of values written, or GC_ERR_INVALID when the
+ * last call kept no such record.
+ */
+int gc_last_round_ns(int64_t* ns, int32_t cap);
 
 /* Text for a gc_status code (static storage). */
 const char* gc_strerror(int code);

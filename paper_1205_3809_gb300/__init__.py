@@ -35,7 +35,8 @@ GC_ERR_TOO_LARGE = -7
 # Every symbol include/gc.h declares.
 EXPORTED = ("gc_color", "gc_color_ex", "gc_color_host", "gc_validate_csr", "gc_strerror",
             "gc_last_cuda_error", "gc_release", "gc_workspace_bytes", "gc_last_launch_count",
-            "gc_last_round_stats", "gc_last_phase_ms", "gc_color_noalloc", "gc_noalloc_capacity_bytes",
+            "gc_last_round_stats", "gc_last_phase_ms", "gc_last_round_ns", "gc_color_noalloc",
+            "gc_noalloc_capacity_bytes",
             "gc_features", "gc_mlp_param_count", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam",
             "gc_priority_keys", "gc_mlp_train_step", "gc_batch_create", "gc_batch_run",
             "gc_batch_launch_graph", "gc_batch_status", "gc_batch_destroy", "gc_batch_workspace_bytes",
@@ -85,7 +86,8 @@ class Options(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("telemetry", ctypes.c_int32),
                 ("narrow_color_limit", ctypes.c_int32), ("tail_volume", ctypes.c_int32),
                 ("batch_mode", ctypes.c_int32), ("local_thread_degree", ctypes.c_int32),
-                ("local_shared_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("local_shared_bytes", ctypes.c_int32), ("barrier_poll_limit", ctypes.c_int32),
+                ("workspace_limit_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 _lib = None
@@ -154,9 +156,10 @@ def _load():
         lib.gc_color_async.restype = ctypes.c_int
         lib.gc_batch_tune.restype = ctypes.c_int
         lib.gc_last_phase_ms.argtypes = [vp, i32]
+        lib.gc_last_round_ns.argtypes = [vp, i32]
         for f in (lib.gc_color, lib.gc_color_ex, lib.gc_color_host, lib.gc_validate_csr,
                   lib.gc_last_cuda_error, lib.gc_release, lib.gc_last_round_stats,
-                  lib.gc_last_phase_ms):
+                  lib.gc_last_phase_ms, lib.gc_last_round_ns):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -351,6 +354,16 @@ def last_phase_ms():
     if m < 0:
         raise GcError(m, "gc_last_phase_ms")
     return [float(ms[i]) for i in range(m)]
+
+
+def last_round_ns(cap: int = 1 << 20):
+    """Per-round durations (ns) of the last call made with telemetry=1 in the persistent
+    launch: entry k-1 is round k's pass (k >= 2); entry 0 is 0."""
+    ns = np.zeros(cap, np.int64)
+    m = int(_load().gc_last_round_ns(ctypes.c_void_p(ns.ctypes.data), cap))
+    if m < 0:
+        raise GcError(m, "gc_last_round_ns")
+    return ns[:m].copy()
 
 
 # ---------------------------------------------------------------- learned priority

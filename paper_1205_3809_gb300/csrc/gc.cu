@@ -48,6 +48,7 @@ struct LastCall {
     int32_t cap = 0;
     const int32_t* d_sizes = nullptr;          // device, workspace
     const unsigned long long* d_vol = nullptr; // device, workspace
+    const unsigned long long* d_ns = nullptr;  // device, workspace (persistent launch with telemetry)
     int timed = 0;
     float ms[4] = {0, 0, 0, 0};
 };
@@ -159,8 +160,16 @@ int ensure_host(void** p, size_t* have, size_t need) {
     return GC_OK;
 }
 
+// A device workspace of `need` bytes, unless the caller's testing limit
+// (workspace_limit_mb) forbids growing the one held to that size: then
+// GC_ERR_OOM, as if cudaMalloc had refused, and the old workspace stays.
+int ensure_device_limited(void** p, size_t* have, size_t need, int32_t limit_mb) {
+    if (limit_mb > 0 && need > *have && need > ((size_t)limit_mb << 20)) return GC_ERR_OOM;
+    return ensure_device(p, have, need);
+}
+
 struct Layout {
-    size_t st, stats, rs, rv, x0, x1, act0, act1, stat, hubs, defer;
+    size_t st, stats, rs, rv, rt, x0, x1, act0, act1, stat, hubs, defer;
     size_t S[2], M[2], H[2], Hc[2], O[2];
     size_t total;
 };
@@ -177,6 +186,7 @@ Layout make_layout(int64_t n, int64_t nnz, size_t elem, const Stats& hs, int64_t
     L.stats = take(sizeof(Stats));
     L.rs = take((size_t)round_cap * sizeof(int32_t));
     L.rv = take((size_t)round_cap * sizeof(unsigned long long));
+    L.rt = take((size_t)(round_cap + 1) * sizeof(unsigned long long));
     L.x0 = take((size_t)n * elem);
     L.x1 = take((size_t)n * elem);
     L.act0 = take((size_t)nnz * sizeof(int32_t));
@@ -365,6 +375,7 @@ int normalise(const gc_options* opt, gc_options* o) {
     if (o->telemetry != 0 && o->telemetry != 1) return GC_ERR_INVALID;
     if (o->batch_mode < 0 || o->batch_mode > 2) return GC_ERR_INVALID;
     if (o->local_shared_bytes != 0 && o->local_shared_bytes < 16384) return GC_ERR_INVALID;
+    if (o->barrier_poll_limit < 0 || o->workspace_limit_mb < 0) return GC_ERR_INVALID;
     return GC_OK;
 }
 
@@ -438,7 +449,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
         max_rounds, std::max<int64_t>(4096, std::min<int64_t>(round_sizes ? round_sizes_cap : 0, 1 << 20))));
 
     // 1. setup scan (its record lives in a small fixed head of the workspace)
-    rc = ensure_device(&dc.ws, &dc.ws_bytes, std::max<size_t>(dc.ws_bytes, 4096));
+    rc = ensure_device_limited(&dc.ws, &dc.ws_bytes, std::max<size_t>(dc.ws_bytes, 4096), o.workspace_limit_mb);
     if (rc != GC_OK) return rc;
     size_t hb = dc.host_bytes;
     rc = ensure_host(&dc.host, &hb, std::max<size_t>(4096, sizeof(RoundState) + (size_t)round_cap * 4));
@@ -473,7 +484,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     for (;;) {
         const size_t elem = bits == 16 ? 2 : 4;
         L = make_layout(n, hs.nnz, elem, hs, round_cap);
-        rc = ensure_device(&dc.ws, &dc.ws_bytes, L.total);
+        rc = ensure_device_limited(&dc.ws, &dc.ws_bytes, L.total, o.workspace_limit_mb);
         if (rc != GC_OK) return rc;
         base = (char*)dc.ws;
         st = (RoundState*)(base + L.st);
@@ -492,6 +503,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
             p.m_max = o.medium_max_degree;
             p.max_rounds = max_rounds;
             p.tail_volume = o.tail_volume;
+            p.barrier_polls = o.barrier_poll_limit > 0 ? (uint32_t)o.barrier_poll_limit : gc::kBarrierMaxPolls;
             p.color_limit = bits == 16 ? (o.narrow_color_limit > 0 ? (uint32_t)o.narrow_color_limit : 0x8000u)
                                        : 0x80000000u;
             p.X0 = (T*)(base + L.x0);
@@ -516,6 +528,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
             p.st = st;
             p.round_sizes = (int32_t*)(base + L.rs);
             p.round_vol = (unsigned long long*)(base + L.rv);
+            p.round_ns = o.telemetry && o.loop_mode == 0 ? (unsigned long long*)(base + L.rt) : nullptr;
             p.round_cap = (int32_t)round_cap;
         };
         NvtxRange range(bits == 16 ? "gc rounds (16-bit colors)" : "gc rounds (32-bit colors)");
@@ -553,6 +566,7 @@ int color_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n, const 
     g_last.cap = (int32_t)round_cap;
     g_last.d_sizes = (const int32_t*)(base + L.rs);
     g_last.d_vol = (const unsigned long long*)(base + L.rv);
+    g_last.d_ns = o.telemetry && o.loop_mode == 0 ? (const unsigned long long*)(base + L.rt) : nullptr;
     g_last.timed = o.telemetry;
     if (o.telemetry) {
         GC_CUDA(cudaEventElapsedTime(&g_last.ms[0], dc.ev[0], dc.ev[1]));
@@ -680,6 +694,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
             p.m_max = o.medium_max_degree;
             p.max_rounds = n;
             p.tail_volume = o.tail_volume;
+            p.barrier_polls = gc::kBarrierMaxPolls;
             p.color_limit = bits == 16 ? 0x8000u : 0x80000000u;
             p.X0 = (T*)(base + L.x0);
             p.X1 = (T*)(base + L.x1);
@@ -703,6 +718,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
             p.st = st;
             p.round_sizes = (int32_t*)(base + L.rs);
             p.round_vol = (unsigned long long*)(base + L.rv);
+            p.round_ns = nullptr;
             p.round_cap = (int32_t)round_cap;
         };
         int64_t launches = 0;
@@ -766,6 +782,7 @@ void fill_workspace(Params<T>& p, char* base, const Layout& L, RoundState* st, i
     p.st = st;
     p.round_sizes = (int32_t*)(base + L.rs);
     p.round_vol = (unsigned long long*)(base + L.rv);
+    p.round_ns = nullptr;
     p.round_cap = (int32_t)round_cap;
 }
 
@@ -930,6 +947,7 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
     p.m_max = b.o.medium_max_degree;
     p.max_rounds = b.o.max_rounds > 0 ? b.o.max_rounds : (int32_t)b.N;
     p.tail_volume = b.o.tail_volume;
+    p.barrier_polls = b.o.barrier_poll_limit > 0 ? (uint32_t)b.o.barrier_poll_limit : gc::kBarrierMaxPolls;
     p.color_limit = b.bits == 16 ? 0x8000u : 0x80000000u;
     p.colors_out = b.colors_out;
     p.settle_round = settle;
@@ -1130,6 +1148,8 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
                    (voff_h[c + 1] - voff_h[c]) + (eoff_h[c + 1] - eoff_h[c]);
         });
         void* ws = nullptr;
+        if (b->o.workspace_limit_mb > 0 && b->ws_bytes > ((size_t)b->o.workspace_limit_mb << 20))
+            return fail(GC_ERR_OOM);
         const cudaError_t e = cudaMalloc(&ws, b->ws_bytes);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1158,6 +1178,8 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
     b->off_flags = h_flags;
     {
         void* ws = nullptr;
+        if (b->o.workspace_limit_mb > 0 && b->ws_bytes > ((size_t)b->o.workspace_limit_mb << 20))
+            return fail(GC_ERR_OOM);
         const cudaError_t e = cudaMalloc(&ws, b->ws_bytes);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1169,7 +1191,7 @@ int batch_create_locked(const int32_t* rowptr_cat, const int32_t* colidx_cat, co
     fail(GC_OK);  // frees the head copy after the stream drains
     // the coloring layout's offsets are relative to its own base
     Layout& L = b->L;
-    size_t* fields[] = {&L.st, &L.stats, &L.rs, &L.rv, &L.x0, &L.x1, &L.act0, &L.act1, &L.stat, &L.hubs,
+    size_t* fields[] = {&L.st, &L.stats, &L.rs, &L.rv, &L.rt, &L.x0, &L.x1, &L.act0, &L.act1, &L.stat, &L.hubs,
                         &L.defer, &L.S[0], &L.S[1], &L.M[0], &L.M[1], &L.H[0], &L.H[1], &L.Hc[0], &L.Hc[1],
                         &L.O[0], &L.O[1]};
     for (size_t* f : fields) *f += lay;
@@ -1278,7 +1300,7 @@ int gc_color_host(const int32_t* rowptr, const int32_t* colidx, int32_t n, const
     cudaStream_t s = (cudaStream_t)stream;
     const size_t b_rp = align_up((size_t)(n + 1) * 4, 256), b_ci = align_up((size_t)nnz * 4 + 4, 256),
                  b_pr = priority ? align_up((size_t)n * 4, 256) : 0, b_co = align_up((size_t)n * 4, 256);
-    rc = ensure_device(&dc.in, &dc.in_bytes, b_rp + b_ci + b_pr + b_co);
+    rc = ensure_device_limited(&dc.in, &dc.in_bytes, b_rp + b_ci + b_pr + b_co, opt ? opt->workspace_limit_mb : 0);
     if (rc != GC_OK) return rc;
     char* base = (char*)dc.in;
     int32_t* d_rp = (int32_t*)base;
@@ -1356,6 +1378,23 @@ int gc_last_round_stats(int32_t* sizes, int64_t* volumes, int32_t cap) {
     if (volumes) {
         volumes[0] = g_last.nnz;
         if (m > 1) GC_CUDA(cudaMemcpy(volumes + 1, g_last.d_vol + 1, (size_t)(m - 1) * 8, cudaMemcpyDeviceToHost));
+    }
+    return m;
+}
+
+int gc_last_round_ns(int64_t* ns, int32_t cap) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_last.valid || !g_last.d_ns || !ns || cap < 0) return GC_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g_last.device) return GC_ERR_INVALID;
+    const int32_t m = std::min({g_last.rounds, cap, g_last.cap});
+    if (m <= 0) return 0;
+    ns[0] = 0;
+    if (m > 1) {
+        // starts of passes 2..m+1 (the one after the last round marks the end)
+        std::vector<unsigned long long> t((size_t)m);
+        GC_CUDA(cudaMemcpy(t.data(), g_last.d_ns + 1, (size_t)m * 8, cudaMemcpyDeviceToHost));
+        for (int32_t k = 2; k <= m; ++k) ns[k - 1] = (int64_t)(t[k - 1] - t[k - 2]);
     }
     return m;
 }

@@ -29,9 +29,10 @@
 // overflow status and the host reruns with 32-bit state.
 //
 // Work is split into warp-sized tasks, binned by the current active length:
-//   S bin (length <= s_max <= 32) and M bin (s_max < length <= m_max <= 256):
-//     32 (S) or 4 (M) worklist entries per task, their lists walked as one
-//     flat range;
+//   S bin (length <= s_max <= 32): 32 worklist entries per task, their lists
+//     walked as one flat range;
+//   M bin (s_max < length <= m_max <= 256): 8 worklist entries per task, each
+//     list read by the whole warp in turn (colors 1..64 in registers);
 //   H bin (length > m_max): one chunk of up to 1024 entries of one list per
 //     task; a list of one chunk is decided by its warp, and the chunks of a
 //     longer list OR their conflict flag and color windows into a per-vertex
@@ -69,11 +70,14 @@ constexpr int kPass1Flat = 256;               // pass 1: longer rows take the pe
 #define GC_MIN_BLOCKS 4
 #endif
 #ifndef GC_MED_PER_TASK
-#define GC_MED_PER_TASK 4
+#define GC_MED_PER_TASK 8
 #endif
 
 constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
-constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task (<= 1024 entries)
+#ifndef GC_M_WARP
+#define GC_M_WARP 1
+#endif
+constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task
 constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
 
@@ -121,6 +125,7 @@ struct RoundState {
     alignas(128) unsigned bar_count;
     alignas(128) unsigned bar_gen;
     alignas(128) int status;
+    int status_at_barrier; // status as the last block to reach the latest barrier saw it
     int rounds;
     int max_color;
     int graph_round;       // loop mode 2: the round the graph's next iteration runs
@@ -145,6 +150,7 @@ struct Params {
     int32_t s_max, m_max;               // length bin limits
     int32_t max_rounds;
     int32_t tail_volume;                // rounds reading <= this many entries run in block 0 alone (< 0: never)
+    uint32_t barrier_polls;             // the grid barrier gives up after this many polls
     uint32_t color_limit;               // a color >= this overflows (16-bit state)
     T* X0;
     T* X1;
@@ -163,6 +169,8 @@ struct Params {
     RoundState* st;
     int32_t* round_sizes;               // device telemetry, round_sizes[k-1] = |U_k|
     unsigned long long* round_vol;      // device telemetry, round_vol[k-1] = entries round k reads
+    unsigned long long* round_ns;       // NULL, or device telemetry: round_ns[k-1] = %globaltimer when
+                                        // round k's pass starts (persistent launch; round_cap + 1 entries)
     int32_t round_cap;
 };
 
@@ -388,7 +396,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // All blocks of a cooperative launch meet here.  Returns false (and sets
 // status = timeout) if the wait gave up; the caller then leaves the loop.
-__device__ __forceinline__ bool grid_barrier(RoundState* st) {
+__device__ __forceinline__ bool grid_barrier(RoundState* st, unsigned max_polls) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -398,6 +406,11 @@ __device__ __forceinline__ bool grid_barrier(RoundState* st) {
         __threadfence();
         const unsigned arrived = atomicAdd(&st->bar_count, 1u);
         if (arrived == gridDim.x - 1) {
+            // every block's writes of this round are in: the status they leave
+            // is the one all blocks act on after the barrier (a block that is
+            // already in the next round may change st->status meanwhile)
+            __threadfence();
+            st->status_at_barrier = *((volatile int*)&st->status);
             atomicExch(&st->bar_count, 0u);
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
@@ -407,7 +420,7 @@ __device__ __forceinline__ bool grid_barrier(RoundState* st) {
             while (*vgen == gen) {
                 __nanosleep(nap);
                 nap = nap < 256 ? nap * 2 : 256;
-                if (++polls >= kBarrierMaxPolls || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                if (++polls >= max_polls || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
                     atomicExch(&st->status, kStatusTimeout);
                     ok = 0;
                     break;
@@ -911,6 +924,126 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     __syncwarp();
 }
 
+// M bin: up to 32 worklist entries per task (lane i holds entry i), taken
+// one vertex at a time by the whole warp: lane l reads entries l, l + 32, ...
+// of the vertex's active list, four batches of 32 in flight.  Colors 1..64
+// collect in per-lane registers (all neighbours, and those found settled)
+// and are OR-reduced once per vertex; colors 65..256 go to the warp's shared
+// windows, where no two vertices meet.  So the lanes never contend on one
+// shared word, which the flat walk does when most of a batch belongs to one
+// long list.  The decisions stay in the lane of their entry, and the task
+// appends its conflicting vertices to the next round with one atomic per
+// bin.
+template <typename T, bool P>  // P: a priority array is given
+__device__ __forceinline__ void vertex_task(const Params<T>& p, const PassIO<T>& io, int4 en,
+                                            FlatSmem& sm, int& maxc, unsigned& vol) {
+    constexpr int kB = 4;  // batches in flight
+    const unsigned lane = lane_id();
+    const bool first = io.first;
+    bool my_conflict = false;
+    int32_t my_kept = 0;
+    unsigned todo = __ballot_sync(kFull, en.x >= 0);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int32_t v = __shfl_sync(kFull, en.x, j);
+        const int32_t b = __shfl_sync(kFull, en.y, j);
+        const int32_t len = __shfl_sync(kFull, en.z, j);
+        const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
+        const uint32_t pv = (P && first) ? __ldg(p.prio + v) : 0u;
+        if (lane < 8u) { sm.dyn[lane] = 0u; sm.stat[lane] = 0u; }
+        __syncwarp();
+        uint32_t rd0 = 0u, rs0 = 0u, rd1 = 0u, rs1 = 0u;  // this lane's colors 1..64 (all, settled)
+        bool conflict = false;
+        int32_t kept = 0;
+        for (int32_t base = 0; base < len; base += 32 * kB) {
+            int32_t w[kB];
+            T c[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int32_t i = base + 32 * u + (int32_t)lane;
+                w[u] = i < len ? ld_row(io.rin + b + i, io.pol_row) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int32_t i = base + 32 * u + (int32_t)lane;
+                c[u] = i < len ? ld_color(io.Xc + (P ? entry_id(w[u]) : w[u]), io.pol_col) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int32_t i = base + 32 * u + (int32_t)lane;
+                const bool in = i < len;
+                const uint32_t col = word_color(c[u]);
+                const bool settled = in && word_settled(c[u]);
+                const int32_t wid = P ? entry_id(w[u]) : w[u];
+                bool pre = false;
+                if constexpr (!P) {
+                    pre = in && col == cv && wid < v;
+                } else if (in && (col == cv || (first && !settled))) {
+                    pre = first ? precedes(p.prio, wid, v, pv) : w[u] < 0;
+                    if (first) w[u] = (int32_t)((uint32_t)wid | (pre ? kPrecBit : 0u));  // the entry kept
+                }
+                if (in) {
+                    if (col == cv && pre) conflict = true;
+                    const unsigned idx = col - 1u;
+                    const uint32_t bit = 1u << (idx & 31u);
+                    if (idx < 32u) {
+                        rd0 |= bit;
+                        rs0 |= settled ? bit : 0u;
+                    } else if (idx < 64u) {
+                        rd1 |= bit;
+                        rs1 |= settled ? bit : 0u;
+                    } else if (idx < 256u) {
+                        atomicOr(&sm.dyn[idx >> 5], bit);
+                        if (settled) atomicOr(&sm.stat[idx >> 5], bit);
+                    }
+                }
+                // survivors, in order, to the next round's list
+                const unsigned kb = __ballot_sync(kFull, in && !settled);
+                if (in && !settled)
+                    st_stream(io.rout + b + kept + __popc(kb & ((1u << lane) - 1u)), w[u], io.pol_row);
+                kept += __popc(kb);
+            }
+        }
+        const bool conf = __any_sync(kFull, conflict);
+        rd0 = __reduce_or_sync(kFull, rd0);
+        rs0 = __reduce_or_sync(kFull, rs0);
+        rd1 = __reduce_or_sync(kFull, rd1);
+        rs1 = __reduce_or_sync(kFull, rs1);
+        __syncwarp();
+        const unsigned q7 = lane & 7u;
+        uint32_t stat = 0u, all = 0u;
+        if (lane < 8u) {
+            const uint32_t old = first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
+            stat = old | sm.stat[q7] | (q7 == 0u ? rs0 : (q7 == 1u ? rs1 : 0u));
+            all = stat | sm.dyn[q7] | (q7 == 0u ? rd0 : (q7 == 1u ? rd1 : 0u));
+        }
+        __syncwarp();
+        if (!conf) {
+            if (lane == 0) settle(p, io, v, cv);
+            maxc = max(maxc, (int)cv);
+        } else {
+            const int ff = window_first_clear(all);
+            const uint32_t color = ff >= 0 ? (uint32_t)ff + 1u : rescan_first_fit(p.rowptr, p.colidx, io.Xc, v);
+            if (lane < 8u) p.stat[(size_t)v * 8 + lane] = stat;
+            if (lane == 0) {
+                recolor(p, io, v, color);
+                vol += (unsigned)kept;
+            }
+        }
+        if ((int)lane == j) {
+            my_conflict = conf;
+            my_kept = kept;
+        }
+    }
+    // next round: same row start, the kept entries; the bin may shrink (never grow)
+    const int4 ne = make_int4(en.x, en.y, my_kept, en.w);
+    const int nb = bin_of(my_kept, p.s_max, p.m_max);
+    warp_append(my_conflict && nb == kBinS, ne, io.next.S, &io.next.cnt[kBinS]);
+    warp_append(my_conflict && nb == kBinM, ne, io.next.M, &io.next.cnt[kBinM]);
+    __syncwarp();
+}
+
 // H bin: one chunk of up to 1024 entries of the vertex at worklist position
 // h.pos, read in sub-blocks of 256 (two halves of 4 entries per lane).  A
 // vertex whose active list fits one chunk is decided by this warp at once;
@@ -1083,6 +1216,10 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
         if (t < nHC) {
             hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
+#if GC_M_WARP
+        } else if (t - nHC < tM) {
+            vertex_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
+#endif
         } else {
             flat_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
         }
@@ -1109,11 +1246,15 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
         const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nH = __ldcg(c + 2),
                        nHC = __ldcg(c + 3);
         const unsigned size = nS + nM + nH;
+        // start of this pass (the last record, for the empty round, marks the end)
+        if (p.round_ns && blockIdx.x == 0 && threadIdx.x == 0 && k - 1 <= p.round_cap)
+            p.round_ns[k - 1] = globaltimer_ns();
         if (size == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) st->rounds = k - 1;
             break;
         }
-        if (__ldcg(&st->status) == kStatusColorOverflow) break;
+        // (not st->status itself: a block already working on this round may set it)
+        if (__ldcg(&st->status_at_barrier) == kStatusColorOverflow) break;
         if (k > p.max_rounds) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->rounds = k - 1;
@@ -1136,7 +1277,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
         run_pass<T, P>(p, k, nS, nM, nHC, maxc, gw, W);
         if (tail) {
             __syncthreads();
-        } else if (!grid_barrier(st)) {
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st->status_at_barrier = *((volatile int*)&st->status);
+            }
+            __syncthreads();
+        } else if (!grid_barrier(st, p.barrier_polls)) {
             break;
         }
     }
