@@ -77,6 +77,9 @@ constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight 
 #ifndef GC_M_WARP
 #define GC_M_WARP 1
 #endif
+#ifndef GC_PREFETCH
+#define GC_PREFETCH 1   // L1 prefetch of the next M vertex's list and the next hub sub-block
+#endif
 constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task
 constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
@@ -750,6 +753,13 @@ struct FlatSmem {
     int32_t vid[32];        // vertex of each lane
 };
 
+// Ask L1 for the line holding a (list entries read soon by this warp).
+__device__ __forceinline__ void prefetch_l1(const void* a) {
+#if GC_PREFETCH
+    asm volatile("prefetch.global.L1 [%0];" :: "l"(a));
+#endif
+}
+
 // Stores of the next round's active lists and static masks: read once, in
 // the next round, so evicted first.
 __device__ __forceinline__ void st_stream(int32_t* a, int32_t x, uint64_t pol) {
@@ -949,6 +959,14 @@ __device__ __forceinline__ void vertex_task(const Params<T>& p, const PassIO<T>&
         const int32_t v = __shfl_sync(kFull, en.x, j);
         const int32_t b = __shfl_sync(kFull, en.y, j);
         const int32_t len = __shfl_sync(kFull, en.z, j);
+        // the next vertex's list comes into L1 while this one is read (lanes 0..8:
+        // one 128-byte line each, the last one for the end of the list)
+        if (todo) {
+            const int jn = __ffs(todo) - 1;
+            const int32_t bn = __shfl_sync(kFull, en.y, jn), ln = __shfl_sync(kFull, en.z, jn);
+            if (lane < 8u && (int32_t)lane * 32 < ln) prefetch_l1(io.rin + bn + 32 * lane);
+            else if (lane == 8u) prefetch_l1(io.rin + bn + ln - 1);
+        }
         const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
         const uint32_t pv = (P && first) ? __ldg(p.prio + v) : 0u;
         if (lane < 8u) { sm.dyn[lane] = 0u; sm.stat[lane] = 0u; }
@@ -1069,6 +1087,8 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     unsigned local = 0;  // survivors written so far (single-chunk vertex)
     uint32_t rd0 = 0u, rs0 = 0u, rd1 = 0u, rs1 = 0u;  // this lane's colors 1..64 (all, settled)
     for (int32_t sb = lo; sb < hi; sb += kHubSub) {
+        // the next sub-block (eight 128-byte lines) comes into L1 meanwhile
+        if (lane < 8u && sb + kHubSub + 32 * (int32_t)lane < hi) prefetch_l1(io.rin + sb + kHubSub + 32 * lane);
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             int32_t w[kHalf];
