@@ -11,6 +11,12 @@ flushed (256 MB write) before every step, outside the step's CUDA events.
 Prints one JSON line (rank 0).  Multi-GPU runs color one replica per rank
 ("replicas only": the method has no exchange step to shard).
 
+Beside it, the same line carries every other configuration of the benchmark
+set, each timed the same way with its own clock record and roofline: the
+learned priority on the same graph, G(n=10,000, m=50,000), R-MAT-ER scale 22,
+the batch of 4,096 graphs, and R-MAT-G scale 23 with index and learned
+priority (`configs`).
+
 --impl reference times the CPU oracle (plain single-threaded C, test
 infrastructure) on the host cores, on bounded samples of the same workload.
 """
@@ -42,9 +48,13 @@ CPU_BASELINE_SCALE = 22
 REFERENCE_STEP_SCALE = 20
 
 # Random 16-bit gathers from an L2-resident table, driven by a streamed int32
-# index array, measured on this machine's GB300 (profiles/l2_random_gather.md).
+# index array (`python bench.py --measure-l2-ceiling`, GB300).
 L2_GATHER_CEILING = 208.0  # G gathers/s, 32 MB table (the scale-24 color state)
 L2_SECTOR_CEILING = 234.0  # G sectors/s: the same run counted in L2 sectors (gathers + index stream)
+# Per-launch ncu counters of the rounds kernel on the bench workload, with the
+# command that took them and the code they belong to.
+PROFILE_JSON = os.path.join(ROOT, "profiles", "rounds_persistent_kernel_rmat_b_s24.json")
+GOLDEN_JSON = os.path.join(ROOT, "tests", "golden", "fullsize.json")
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -274,12 +284,11 @@ def fixed_bytes_call(n, nnz, sizes, degree_vols):
 
 def stored_degree_volumes(n, nnz, sizes):
     """Per-round degree volumes of this workload as the oracle computed them
-    (tests/golden/fullsize.json, written by tests/golden/make_fullsize.py), when
-    the run's |U_k| are the stored ones; else None."""
-    path = os.path.join(ROOT, "tests", "golden", "fullsize.json")
-    if not os.path.exists(path):
+    (stored with its other full-size results by tests/golden/make_fullsize.py),
+    when the run's |U_k| are the stored ones; else None."""
+    if not os.path.exists(GOLDEN_JSON):
         return None
-    for entry in json.load(open(path)).values():
+    for entry in json.load(open(GOLDEN_JSON)).values():
         if (entry.get("n") == n and entry.get("nnz") == nnz and entry.get("round_sizes") == [int(x) for x in sizes]
                 and "round_degree_volumes" in entry):
             return entry["round_degree_volumes"]
@@ -338,35 +347,14 @@ def kernel_code_hash(path: str) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
-def load_profile_fields(kernel_src):
-    """Per-launch counters of the rounds kernel from the committed ncu summary
-    (`- key: value` lines), or {} if the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "rounds_persistent_kernel_rmat_b.md")
+def load_profile(kernel_src, path=PROFILE_JSON):
+    """The per-launch ncu counters of the rounds kernel (with the command that
+    took them), or {} if that file is missing or the kernel's code has changed
+    since the capture."""
     if not os.path.exists(path):
         return {}
-    want = kernel_code_hash(kernel_src)
-    fields = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            fields[k.strip()] = v.strip().strip("`")
-    return fields if fields.get("kernel_code_sha256") == want else {}
-
-
-def load_traffic(kernel_src):
-    """Per-launch DRAM bytes of the rounds kernel (full size), or None."""
-    try:
-        return int(load_profile_fields(kernel_src)["traffic_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
-
-
-def load_l2_sectors(kernel_src):
-    """Per-launch L2 sectors of the rounds kernel at full size (a one-pass capture), or None."""
-    try:
-        return int(load_profile_fields(kernel_src)["l2_sectors_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
+    d = json.load(open(path))
+    return d if d.get("kernel_code_sha256") == kernel_code_hash(kernel_src) else {}
 
 
 def peaks():
@@ -448,10 +436,13 @@ def run_ours(args):
     kms = statistics.mean(kernel_ms)
     achieved = alg_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic = load_traffic(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
+    prof = load_profile(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
+    per_launch = prof.get("per_launch", {})
+    traffic = (per_launch["dram__bytes_read.sum"] + per_launch["dram__bytes_write.sum"]
+               if "dram__bytes_read.sum" in per_launch and "dram__bytes_write.sum" in per_launch else None)
+    sectors = per_launch.get("lts__t_sectors.sum")
     gathers = gathers_rounds(vols)
     gather_rate = gathers / (kms / 1e3) / 1e9
-    sectors = load_l2_sectors(os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "gc_device.cuh"))
 
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
@@ -478,6 +469,11 @@ def run_ours(args):
 
     learned = None if args.no_learned else measure_learned(gcpkg, rp, ci, g, flush, stream, args)
     asynchronous = None if args.no_learned else measure_async(gcpkg, rp, ci, g, flush, stream, args)
+    configs = None
+    if not args.no_configs and world == 1:
+        del rp, ci
+        torch.cuda.empty_cache()
+        configs = measure_configs(gcpkg, flush, stream, args, gpu_id)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -513,6 +509,9 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "rounds_persistent_kernel",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": ({"file": os.path.relpath(PROFILE_JSON, ROOT),
+                                             "command": prof.get("command"), "workload": prof.get("workload")}
+                                            if traffic is not None else None),
                          "algorithmic_bytes": alg_bytes, "kernel_ms": kms,
                          "accounting": ("whole rows: fixed per-round bytes of the method (worklist, rowptr, "
                                         "colidx and neighbour colors of every row of U_k, own color, appends)"
@@ -527,10 +526,11 @@ def run_ours(args):
                              "count": sectors, "achieved_G_per_s": sectors / (kms / 1e3) / 1e9,
                              "ceiling_G_per_s": L2_SECTOR_CEILING,
                              "frac": sectors / (kms / 1e3) / 1e9 / L2_SECTOR_CEILING,
-                             "source": "lts__t_sectors.sum of one full-size launch (profiles/)"}},
+                             "source": os.path.relpath(PROFILE_JSON, ROOT)}},
             "cpu_baseline": cpu,
             "learned": learned,
             "asynchronous": asynchronous,
+            "configs": configs,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -538,6 +538,105 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def config_roofline(n, nnz, sizes, vols, kms):
+    """Roofline of the rounds kernel for one configuration: the fixed whole-row
+    bytes when the oracle's degree volumes of that workload are stored, else
+    this implementation's active-entry bytes (said in `accounting`)."""
+    peak, peak_kind = peaks()
+    degree_vols = stored_degree_volumes(n, nnz, sizes)
+    alg = fixed_bytes_rounds(sizes, degree_vols) if degree_vols else algorithmic_bytes_rounds(sizes, vols, 2)
+    achieved = alg / (kms / 1e3) / 1e9 if kms > 0 else None
+    return {"bound": "hbm", "kernel": "rounds_persistent_kernel", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": None if achieved is None else achieved / peak,
+            "traffic": None, "algorithmic_bytes": alg, "kernel_ms": kms,
+            "accounting": ("whole rows: fixed per-round bytes of the method (oracle degree volumes)"
+                           if degree_vols else "active entries (this implementation's reads)")}
+
+
+def time_config(gcpkg, g, workload, flush, stream, steps, warmup, gpu_id, learned=False):
+    """One configuration of the benchmark set, timed like the main line: CUDA
+    events around each step on the launching stream, L2 flushed before each
+    step outside the events, nvidia-smi clocks sampled over the timed steps.
+    learned: the step is features -> network -> keys -> coloring under the keys
+    (the shipped network), as one step."""
+    import torch
+    dev = flush.device
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    opts = {"telemetry": 1}
+    if learned:
+        params = gcpkg.load_priority_model(device=dev)
+        feats = torch.empty((g.n, 6), dtype=torch.float32, device=dev)
+        scores = torch.empty(g.n, dtype=torch.float32, device=dev)
+        keys = torch.empty(g.n, dtype=torch.int32, device=dev)
+
+    def step():
+        if learned:
+            gcpkg.features(rp, ci, out=feats, stream=stream)
+            gcpkg.mlp_forward(params, feats, out=scores, stream=stream)
+            gcpkg.priority_keys(scores, out=keys, stream=stream)
+            return gcpkg.color(rp, ci, keys, out=out, options=opts, stream=stream)
+        return gcpkg.color(rp, ci, out=out, options=opts, stream=stream)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    t0 = time.time()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kernel_ms, launches = [], 0
+    for a, e in evs:
+        flush.zero_()
+        a.record(stream)
+        res = step()
+        e.record(stream)
+        kernel_ms.append(gcpkg.last_phase_ms()[2])
+        launches += gcpkg.last_launch_count() + (3 if learned else 0)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop(t0, time.time())
+    ms = statistics.mean(a.elapsed_time(e) for a, e in evs)
+    sizes, vols = gcpkg.last_round_stats()
+    kms = statistics.mean(kernel_ms)
+    return {"workload": workload, "n": g.n, "m": g.m, "max_degree": g.max_degree,
+            "priority": "learned (features, network, keys inside the step)" if learned else "index (plain)",
+            "value": g.m / (ms / 1e3), "unit": "edges/s", "ms_per_step": ms, "steps": steps,
+            "ncolors": res.ncolors, "rounds": res.rounds, "gpu_launches": launches,
+            "roofline": config_roofline(g.n, g.nnz, sizes, vols, kms), "clocks": clocks}
+
+
+def measure_configs(gcpkg, flush, stream, args, gpu_id):
+    """The other configurations of the benchmark set, each timed on its own."""
+    steps, warmup = max(5, args.steps // 2), 3
+    out = {}
+    t = time.time()
+    g = gg.gnm(10000, 50000, 1)
+    out["c0_gnm_10k_50k"] = time_config(gcpkg, g, "G(n=10,000, m=50,000), seed 1; index priority", flush, stream,
+                                        steps, warmup, gpu_id)
+    g = gg.rmat(22, EF, gg.RMAT_ER, 2)
+    out["c1_rmat_er_s22"] = time_config(
+        gcpkg, g, "R-MAT-ER scale 22: 4,194,304 vertices, edge factor 8, (0.25,0.25,0.25,0.25), seed 2, "
+        "ids permuted; index priority", flush, stream, steps, warmup, gpu_id)
+    g = gg.rmat(23, EF, gg.RMAT_G, 5)
+    wl = "R-MAT-G scale 23: 8,388,608 vertices, edge factor 8, (0.45,0.15,0.15,0.25), seed 5, ids permuted"
+    c4 = {"plain": time_config(gcpkg, g, wl + "; index priority", flush, stream, steps, warmup, gpu_id)}
+    if os.path.exists(gcpkg.PRIORITY_MODEL):
+        c4["learned"] = time_config(gcpkg, g, wl + "; learned priority", flush, stream, steps, warmup, gpu_id,
+                                    learned=True)
+        c4["learned_no_more_colors_than_plain"] = c4["learned"]["ncolors"] <= c4["plain"]["ncolors"]
+    out["c4_rmat_g_s23"] = c4
+    del g
+    log(f"configs c0/c1/c4 in {time.time() - t:.1f}s")
+    if not args.no_batch:
+        t = time.time()
+        out["c3_batched_4096"] = measure_batched(gcpkg, args.batch_graphs, flush, stream, steps, warmup, gpu_id,
+                                                 options={}, use_graph=True, e2e_steps=3)
+        log(f"config c3 in {time.time() - t:.1f}s")
+    return out
 
 
 def measure_learned(gcpkg, rp, ci, g, flush, stream, args):
@@ -617,70 +716,78 @@ def measure_async(gcpkg, rp, ci, g, flush, stream, args):
             "note": "Phase 1 reads live colors (the paper's shared-memory form); colors vary run to run"}
 
 
-def run_batched(args):
-    """The batched workload: 4,096 graphs (sizes log-uniform in [1,000, 200,000]; 2-D
-    grids, random geometric graphs and R-MAT-G in turn; seed 4) colored in one
-    persistent launch replayed as a CUDA graph, options picked by the autotuner."""
+def measure_batched(gcpkg, count, flush, stream, steps, warmup, gpu_id, options, use_graph=True, e2e_steps=3,
+                    cpu_baseline=False):
+    """The batched workload: `count` graphs (sizes log-uniform in [1,000, 200,000];
+    2-D grids, random geometric graphs and R-MAT-G in turn; seed 4) colored in
+    one persistent launch, replayed as a CUDA graph; each step timed with CUDA
+    events (L2 flushed before it), clocks sampled over the timed steps."""
     import torch
-    import paper_1205_3809_gb300 as gcpkg
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    gcpkg.library()
+    dev = flush.device
     t = time.time()
-    gs = gg.batch_mix(args.batch_graphs, 4)
+    gs = gg.batch_mix(count, 4)
     rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
     m_total = int(sum(g.m for g in gs))
     log(f"batch of {len(gs)} graphs: N={voff[-1]} nnz={eoff[-1]} m={m_total} generated in {time.time() - t:.1f}s")
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    stream = torch.cuda.current_stream(dev)
-    t = time.time()
-    if args.no_autotune:
-        best, table = ({"batch_mode": args.batch_mode} if args.batch_mode else {}), []
-    else:
-        best, table = gcpkg.autotune_batch(rp_d, ci_d, voff, eoff, reps=2)
-    log(f"autotune {time.time() - t:.1f}s: best {best}")
-    use_graph = args.batch_launch == "graph"
-    b = gcpkg.Batch(rp_d, ci_d, voff, eoff, options=best)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
+    b = gcpkg.Batch(rp_d, ci_d, voff, eoff, options=options)
+    for _ in range(warmup):
         flush.zero_()
         b.run(graph=use_graph)
     b.status()
-    props = torch.cuda.get_device_properties(dev)
-    sampler = ClockSampler("GPU-" + str(props.uuid) if getattr(props, "uuid", None) else "0")
+    sampler = ClockSampler(gpu_id)
     time.sleep(0.3)
     torch.cuda.synchronize(dev)
     t0 = time.time()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, e in evs:
         flush.zero_()
         a.record(stream)
         b.run(graph=use_graph)
         e.record(stream)
     torch.cuda.synchronize(dev)
-    t1 = time.time()
-    clocks = sampler.stop(t0, t1)
+    clocks = sampler.stop(t0, time.time())
     max_rounds, max_colors = b.status()
     ms = [a.elapsed_time(e) for a, e in evs]
-    total_s = sum(ms) / 1e3
+    run_s = sum(ms) / 1e3 / len(ms)
     sizes, vols, bits = b.round_stats()
     N, NNZ = int(voff[-1]), int(eoff[-1])
-    if b.mode == 2:
-        # this mode reads whole rows, so its round volumes are the fixed accounting's vol_k
-        alg_bytes = fixed_bytes_call(N, NNZ, sizes, vols)
-        moved_bytes = algorithmic_bytes_batch_blocks(N, sizes, vols)
-    else:
-        alg_bytes = moved_bytes = algorithmic_bytes_batch(N, NNZ, sizes, vols, bits // 8)
-    run_s = total_s / len(evs)
     peak, peak_kind = peaks()
-    gathers = gathers_rounds(vols)
+    if b.mode == 2:
+        # device memory this mode moves (its colors live in shared memory) sets the fraction;
+        # the method's fixed whole-row bytes (this mode reads whole rows, so its volumes are
+        # the accounting's vol_k) go beside it
+        moved = algorithmic_bytes_batch_blocks(N, sizes, vols)
+        fixed = fixed_bytes_call(N, NNZ, sizes, vols)
+        roof = {"bound": "hbm", "kernel": "whole run (byte-color and 32-bit passes of batch_local_kernel)",
+                "batch_mode": 2, "achieved": moved / run_s / 1e9, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": moved / run_s / 1e9 / peak, "traffic": None,
+                "algorithmic_bytes": moved, "run_ms": 1e3 * run_s, "color_state_bits": bits,
+                "accounting": "device-memory bytes this mode moves: rows, worklists, final colors",
+                "fixed_whole_row": {"algorithmic_bytes": fixed, "achieved": fixed / run_s / 1e9,
+                                    "frac": fixed / run_s / 1e9 / peak,
+                                    "note": "the method's whole-row bytes over every graph, neighbour colors "
+                                            "counted although this mode reads them from shared memory"},
+                "shared_memory_gathers": {"count": int(sum(int(x) for x in vols)),
+                                          "achieved_G_per_s": sum(int(x) for x in vols) / run_s / 1e9}}
+    else:
+        alg = algorithmic_bytes_batch(N, NNZ, sizes, vols, bits // 8)
+        gathers = gathers_rounds(vols)
+        roof = {"bound": "hbm", "kernel": "whole run (rebase, pass 1, rounds, reduce)", "batch_mode": 1,
+                "achieved": alg / run_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": alg / run_s / 1e9 / peak, "traffic": None, "algorithmic_bytes": alg,
+                "run_ms": 1e3 * run_s, "color_state_bits": bits,
+                "accounting": "this implementation's reads and writes",
+                "l2_gathers": {"count": gathers, "achieved_G_per_s": gathers / run_s / 1e9,
+                               "ceiling_G_per_s": L2_GATHER_CEILING,
+                               "frac": gathers / run_s / 1e9 / L2_GATHER_CEILING}}
+    roof["round_sizes"] = [int(x) for x in sizes]
     # end to end: host buffers in, colors and per-graph counts out
     h_rp, h_ci = torch.from_numpy(rp).pin_memory(), torch.from_numpy(ci).pin_memory()
-    h_col = torch.empty(int(voff[-1]), dtype=torch.int32).pin_memory()
+    h_col = torch.empty(N, dtype=torch.int32).pin_memory()
     h_nc = torch.empty(len(gs), dtype=torch.int32).pin_memory()
     e_ms = []
-    for _ in range(max(3, args.steps // 3)):
+    for _ in range(e2e_steps):
         flush.zero_()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -692,54 +799,67 @@ def run_batched(args):
         e.record(stream)
         e.synchronize()
         e_ms.append(a.elapsed_time(e))
-    line = {
-        "metric": "edges colored/sec, batch of 4,096 graphs on 1 GB300", "value": len(evs) * m_total / total_s,
-        "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"batch of {len(gs)} graphs, sizes log-uniform in [1,000, 200,000], 2-D grids / "
-                               "random geometric (avg degree 8) / R-MAT-G edge factor 8 in turn, seed 4; one "
-                               "persistent launch " + ("replayed as a CUDA graph" if use_graph else
-                                                        "(plain launches)"),
-                   "graphs": len(gs), "N": int(voff[-1]), "nnz": int(eoff[-1]), "m": m_total,
-                   "options": best, "max_rounds": max_rounds, "max_colors": max_colors,
-                   "workspace_bytes": b.workspace_bytes,
-                   "l2": "inputs larger than L2 and L2 flushed (256 MB write) before every step"},
-        "roofline": {"bound": "hbm",
-                     "kernel": ("whole run (byte-color and 32-bit passes of batch_local_kernel)" if b.mode == 2
-                                else "whole run (rebase, pass 1, rounds, reduce)"),
-                     "batch_mode": b.mode,
-                     "achieved": alg_bytes / run_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": alg_bytes / run_s / 1e9 / peak, "traffic": None,
-                     "algorithmic_bytes": alg_bytes, "run_ms": 1e3 * run_s, "color_state_bits": bits,
-                     "accounting": ("whole rows: fixed bytes of the method over every graph (neighbour colors "
-                                    "counted as the method's reads, though this mode keeps them in shared memory)"
-                                    if b.mode == 2 else "this implementation's reads and writes"),
-                     "device_memory_bytes": moved_bytes,
-                     "round_sizes": [int(x) for x in sizes],
-                     **({"shared_memory_gathers": {
-                         "count": int(sum(int(x) for x in vols)),
-                         "achieved_G_per_s": sum(int(x) for x in vols) / run_s / 1e9,
-                         "note": "neighbour colors read from shared memory, all rounds"}} if b.mode == 2 else
-                        {"l2_gathers": {"count": gathers, "achieved_G_per_s": gathers / run_s / 1e9,
-                                        "ceiling_G_per_s": L2_GATHER_CEILING,
-                                        "frac": gathers / run_s / 1e9 / L2_GATHER_CEILING}})},
-        "autotune": [{"options": o, "ms": round(t_, 3)} for o, t_ in table],
+    out = {
+        "workload": (f"batch of {len(gs)} graphs, sizes log-uniform in [1,000, 200,000], 2-D grids / random "
+                     "geometric (avg degree 8) / R-MAT-G edge factor 8 in turn, seed 4; one persistent launch "
+                     + ("replayed as a CUDA graph" if use_graph else "(plain launches)")),
+        "graphs": len(gs), "N": N, "nnz": NNZ, "m": m_total,
+        "value": m_total / run_s, "unit": "edges/s", "ms_per_step": 1e3 * run_s, "steps": steps,
+        "options": options, "batch_mode": b.mode, "max_rounds": max_rounds, "max_colors": max_colors,
+        "workspace_bytes": b.workspace_bytes, "gpu_launches": b.launch_count * steps,
+        "l2": "inputs larger than L2 and L2 flushed (256 MB write) before every step",
+        "roofline": roof, "clocks": clocks,
         "e2e": {"value": m_total / (statistics.mean(e_ms) / 1e3), "unit": "edges/s",
-                "h2d_bytes_per_step": 4 * (rp.size + ci.size), "d2h_bytes_per_step": 4 * (int(voff[-1]) + len(gs)),
+                "h2d_bytes_per_step": 4 * (rp.size + ci.size), "d2h_bytes_per_step": 4 * (N + len(gs)),
                 "ms_per_step": statistics.mean(e_ms)},
-        "gpu_launches": b.launch_count * args.steps,
-        "clocks": clocks,
-        "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(gs),
     }
-    print(json.dumps(line), flush=True)
+    if cpu_baseline:
+        out["cpu_baseline"] = batch_cpu_baseline(gs)
     b.close()
+    return out
+
+
+def run_batched(args):
+    """`--batched`: the batch of 4,096 graphs as its own JSON line, options picked
+    by the autotuner (unless --no-autotune)."""
+    import torch
+    import paper_1205_3809_gb300 as gcpkg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    gcpkg.library()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else "0"
+    best, table = ({"batch_mode": args.batch_mode} if args.batch_mode else {}), []
+    if not args.no_autotune:
+        gs = gg.batch_mix(args.batch_graphs, 4)
+        rp, ci, voff, eoff = gcpkg.pack_batch((g.rowptr, g.colidx) for g in gs)
+        t = time.time()
+        best, table = gcpkg.autotune_batch(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), voff, eoff,
+                                           reps=2)
+        log(f"autotune {time.time() - t:.1f}s: best {best}")
+        del gs, rp, ci
+        torch.cuda.empty_cache()
+    r = measure_batched(gcpkg, args.batch_graphs, flush, stream, args.steps, args.warmup, gpu_id, best,
+                        use_graph=args.batch_launch == "graph", e2e_steps=max(3, args.steps // 3),
+                        cpu_baseline=not args.no_cpu_baseline)
+    line = {"metric": "edges colored/sec, batch of 4,096 graphs on 1 GB300", "value": r["value"], "unit": "edges/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "graphs", "N", "nnz", "m", "options", "batch_mode", "max_rounds",
+                                         "max_colors", "workspace_bytes", "l2")},
+            "roofline": r["roofline"], "autotune": [{"options": o, "ms": round(t_, 3)} for o, t_ in table],
+            "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+            "cpu_baseline": r.get("cpu_baseline")}
+    print(json.dumps(line), flush=True)
 
 
 def measure_l2_ceiling():
     import shutil
     import tempfile
-    src = os.path.join(ROOT, "paper_1205_3809_gb300", "csrc", "l2_gather_probe.cu")
+    src = os.path.join(ROOT, "l2_gather_probe.cu")
     tmp = tempfile.mkdtemp(prefix="gc_probe_")
     exe = os.path.join(tmp, "l2_gather_probe")
     try:
@@ -758,6 +878,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="time only the main workload (no c0/c1/c3/c4 sub-objects)")
+    ap.add_argument("--no-batch", action="store_true", help="leave the batched configuration out of `configs`")
     ap.add_argument("--batched", action="store_true",
                     help="time the 4,096-graph batched workload instead (one JSON line)")
     ap.add_argument("--batch-graphs", type=int, default=4096)

@@ -244,9 +244,13 @@ int64_t gc_last_launch_count(void);
  * stack.  The first call on each device looks up that array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call shares the array and it keeps the last call's
- * contents; each call clears what must start at zero, but calls that overlap
- * on the GPU (on different streams) race on it and must not be issued.
- * Calls from several host threads are serialised.
+ * contents; each call clears what must start at zero.  Two calls that ran
+ * on the GPU at the same time would race on the array; that cannot happen
+ * here, because the call synchronises `stream` before it returns (it reads
+ * the round count back) and calls from several host threads are serialised.
+ * gc_last_round_stats, gc_last_round_ns and gc_last_phase_ms report nothing
+ * after this call (GC_ERR_INVALID); gc_last_launch_count counts its kernel
+ * launches.
  * Returns GC_ERR_TOO_LARGE when the graph needs more workspace than the
  * array holds (roughly 70 bytes per vertex plus 8 per adjacency entry), and
  * otherwise the codes gc_color returns.

@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle``: the library never imports
 it.  The paper colors in index order (Sec. 3.2) and cites vertex orderings for
 Greedy (smallest-last, largest-first: Sec. 1, Sec. 3.1); the learned priority
 replaces the index by a key that a small network computes from per-vertex
-features, trained to place each vertex where the smallest-last ordering puts it
-(on a log scale of the position).
+features, trained to place each vertex where an ordering the oracle computes
+puts it (on a log scale of the position): smallest-last or largest-first,
+whichever lets serial Greedy use fewer colors on that graph.
 
 ``features`` and ``mlp_forward`` wrap ``learned.c`` (the score decides the order
 of the keys, so it is computed in the network's own precision: bf16 operands,
@@ -19,7 +20,7 @@ import ctypes
 
 import numpy as np
 
-from . import _csr, _load, _ptr, smallest_last_order
+from . import _csr, _load, _ptr, greedy, largest_first_order, smallest_last_order
 
 N_IN, N_HIDDEN = 6, 32
 OFF_W1 = 0
@@ -144,16 +145,41 @@ def learned_keys(rowptr, colidx, params) -> np.ndarray:
     return priority_keys(mlp_forward(params, features(rowptr, colidx)))
 
 
-def smallest_last_targets(rowptr, colidx) -> np.ndarray:
-    """Training target of each vertex: log2(1 + its position in the smallest-last
-    ordering), position 0 = colored first; float32 [n].
+def position_targets(order) -> np.ndarray:
+    """Training target of each vertex: log2(1 + its position in `order`),
+    position 0 = colored first; float32 [n].
 
     The log spreads the front of the ordering (the dense core, which decides the
     number of colors) over as wide a range as the rest, and keeps the target of
     the first vertices the same in graphs of any size.
     """
-    order, _ = smallest_last_order(rowptr, colidx)
+    order = np.asarray(order)
     n = order.shape[0]
     pos = np.empty(n, np.float64)
     pos[order] = np.arange(n, dtype=np.float64)
     return np.log2(1.0 + pos).astype(np.float32)
+
+
+def smallest_last_targets(rowptr, colidx) -> np.ndarray:
+    """position_targets of the smallest-last ordering."""
+    order, _ = smallest_last_order(rowptr, colidx)
+    return position_targets(order)
+
+
+def ordering_targets(rowptr, colidx):
+    """Training targets from the two vertex orderings the paper cites for Greedy
+    (Sec. 1, Sec. 3.1): smallest-last and largest-first, both computed here.
+    Each is colored by Algorithm 1 (serial Greedy) in its order, and the one that
+    uses fewer colors labels the graph; on a tie, smallest-last (its color count
+    is bounded by the degeneracy + 1).
+
+    Returns (position_targets of the chosen ordering, {"ordering": its name,
+    "colors": {"smallest_last": c, "largest_first": c}}).
+    """
+    sl, _ = smallest_last_order(rowptr, colidx)
+    lf = largest_first_order(rowptr)
+    c_sl = greedy(rowptr, colidx, sl)[1]
+    c_lf = greedy(rowptr, colidx, lf)[1]
+    order, name = (lf, "largest_first") if c_lf < c_sl else (sl, "smallest_last")
+    return position_targets(order), {"ordering": name,
+                                     "colors": {"smallest_last": int(c_sl), "largest_first": int(c_lf)}}

@@ -642,6 +642,10 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
                          int32_t* rounds, cudaStream_t s) {
     if (n < 0 || !ncolors || !rounds) return GC_ERR_INVALID;
     if (n > 0 && (!rowptr || !colors_out)) return GC_ERR_INVALID;
+    // the telemetry queries describe gc_color / gc_color_ex calls only; this call
+    // keeps no per-round record, so it leaves them with nothing to report
+    g_last.valid = 0;
+    g_last_launches = 0;
     if (n == 0) {
         *ncolors = 0;
         *rounds = 0;
@@ -666,6 +670,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
         GC_CUDA(cudaMemcpyAsync(&hs, stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
         GC_CUDA(cudaStreamSynchronize(s));
     }
+    int64_t launches = 1;
     if (hs.bad || hs.nnz < 0) return GC_ERR_BAD_GRAPH;
     if (hs.nnz > 0 && !colidx) return GC_ERR_INVALID;
 
@@ -721,7 +726,6 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
             p.round_ns = nullptr;
             p.round_cap = (int32_t)round_cap;
         };
-        int64_t launches = 0;
         if (bits == 16) {
             Params<uint16_t> p;
             fill(p);
@@ -743,6 +747,7 @@ int color_noalloc_locked(const int32_t* rowptr, const int32_t* colidx, int32_t n
         if (hst.status == gc::kStatusMaxRounds) return GC_ERR_MAX_ROUNDS;
         *rounds = hst.rounds;
         *ncolors = hst.max_color;
+        g_last_launches = launches;
         return GC_OK;
     }
 }

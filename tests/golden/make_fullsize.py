@@ -22,6 +22,8 @@ import graphgen as gg  # noqa: E402
 import oracle  # noqa: E402
 
 WORKLOADS = {
+    # R-MAT-ER scale 22 (4,194,304 vertices, edge factor 8), (0.25,0.25,0.25,0.25), seed 2
+    "rmat_er_s22_seed2": lambda: gg.rmat(22, 8, gg.RMAT_ER, 2),
     # R-MAT-B scale 24 (16,777,216 vertices, edge factor 8), (0.55,0.15,0.15,0.15), seed 3
     "rmat_b_s24_seed3": lambda: gg.rmat(24, 8, gg.RMAT_B, 3),
     # R-MAT-G scale 23 (8,388,608 vertices, edge factor 8), (0.45,0.15,0.15,0.25), seed 5
@@ -34,7 +36,7 @@ WORKLOADS = {
 
 
 # learned priority: the shipped network's keys (computed by the oracle), then the same rounds
-LEARNED = {"rmat_b_s24_seed3_learned": "rmat_b_s24_seed3"}
+LEARNED = {"rmat_b_s24_seed3_learned": "rmat_b_s24_seed3", "rmat_g_s23_seed5_learned": "rmat_g_s23_seed5"}
 
 
 def learned_keys(g):

@@ -59,3 +59,31 @@ def test_options_struct_mirrors_header():
     assert names == [f for f, _ in m.Options._fields_]
     width = sum(int(n) if n else 1 for _, n in fields)
     assert ctypes.sizeof(m.Options) == 4 * width
+
+
+def test_color_batched_rejects_bad_offsets_before_any_device_call(lib):
+    """gc_color_batched (the one-call batch entry point) checks its host offset
+    arrays first: NULL offsets, offsets that do not start at 0 or decrease, and a
+    loop_mode the batch kernels do not have are GC_ERR_INVALID, with no GPU."""
+    import paper_1205_3809_gb300 as m
+    i64 = ctypes.c_int64
+    f = lib.gc_color_batched
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7 + \
+                 [ctypes.POINTER(m.Options)]
+
+    def call(voff, eoff, g, opt=None):
+        va = (i64 * len(voff))(*voff) if voff is not None else None
+        ea = (i64 * len(eoff))(*eoff) if eoff is not None else None
+        return f(ctypes.cast(va, ctypes.c_void_p) if va else None, ctypes.cast(ea, ctypes.c_void_p) if ea else None,
+                 g, None, None, None, None, None, None, None, ctypes.byref(opt) if opt else None)
+
+    assert call(None, None, 1) == m.GC_ERR_INVALID
+    assert call([0, 4], None, 1) == m.GC_ERR_INVALID
+    assert call([1, 4], [0, 6], 1) == m.GC_ERR_INVALID           # vertex offsets must start at 0
+    assert call([0, 4, 3], [0, 6, 8], 2) == m.GC_ERR_INVALID     # decreasing vertex offsets
+    assert call([0, 4, 5], [0, 6, 2], 2) == m.GC_ERR_INVALID     # decreasing edge offsets
+    assert call([0, 4], [0, 6], -1) == m.GC_ERR_INVALID          # negative graph count
+    o = m.Options()
+    o.loop_mode = 1
+    assert call([0, 4], [0, 6], 1, o) == m.GC_ERR_INVALID

@@ -1,5 +1,6 @@
 """Host-side accounting of bench.py (no GPU): algorithmic bytes and gathers per
 run, and the code hash that ties committed ncu counters to the kernel source."""
+import json
 import os
 import sys
 
@@ -96,3 +97,20 @@ def test_golden_degree_volumes_follow_their_definition():
         r = oracle.iterative(g.rowptr, g.colidx)
         want = [int(g.degrees[r.settle_round >= k].sum()) for k in range(1, r.rounds + 1)]
         assert make_fullsize.degree_volumes(g, r) == want
+
+
+def test_profile_counters_only_for_the_captured_code(tmp_path):
+    """load_profile returns the stored ncu counters only while the kernel source
+    (comments aside) is the one they were captured from."""
+    src = tmp_path / "k.cuh"
+    src.write_text("__global__ void k() { int x = 1; }\n")
+    prof = tmp_path / "p.json"
+    prof.write_text(json.dumps({"kernel_code_sha256": bench.kernel_code_hash(str(src)), "command": "ncu ...",
+                                "per_launch": {"dram__bytes_read.sum": 5, "dram__bytes_write.sum": 7}}))
+    d = bench.load_profile(str(src), str(prof))
+    assert d["per_launch"]["dram__bytes_read.sum"] == 5
+    src.write_text("// a comment\n__global__ void k() { int x = 1; }\n")
+    assert bench.load_profile(str(src), str(prof))["command"] == "ncu ..."
+    src.write_text("__global__ void k() { int x = 2; }\n")
+    assert bench.load_profile(str(src), str(prof)) == {}
+    assert bench.load_profile(str(src), str(tmp_path / "missing.json")) == {}

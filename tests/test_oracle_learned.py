@@ -274,6 +274,27 @@ def test_smallest_last_targets_are_log_positions():
     assert t[order[0]] == 0.0 and t[order[1]] == 1.0 and t[order[3]] == 2.0
 
 
+@pytest.mark.parametrize("seed,winner", [
+    (10, "largest_first"),   # G(40, 120) seeds where serial Greedy does better in largest-first order,
+    (12, "smallest_last"),   # better in smallest-last order,
+    (1, "smallest_last"),    # and equally well (a tie labels by smallest-last)
+])
+def test_ordering_targets_label_by_fewer_greedy_colors(seed, winner):
+    """The label rule: both orderings colored by Algorithm 1, the one with fewer
+    colors gives the targets (log2(1 + position)), smallest-last on a tie."""
+    g = gg.gnm(40, 120, seed)
+    t, lab = L.ordering_targets(g.rowptr, g.colidx)
+    sl, _ = oracle.smallest_last_order(g.rowptr, g.colidx)
+    lf = oracle.largest_first_order(g.rowptr)
+    c_sl = oracle.greedy(g.rowptr, g.colidx, sl)[1]
+    c_lf = oracle.greedy(g.rowptr, g.colidx, lf)[1]
+    assert lab["colors"] == {"smallest_last": c_sl, "largest_first": c_lf}
+    assert (c_lf < c_sl) == (winner == "largest_first") and (c_sl < c_lf) == (seed == 12)
+    assert lab["ordering"] == winner
+    order = lf if winner == "largest_first" else sl
+    assert np.array_equal(t[order], np.log2(1.0 + np.arange(g.n)).astype(np.float32))
+
+
 def test_learned_keys_compose():
     g = gg.rmat(9, 8, gg.RMAT_G, 4)
     p = _params(51)

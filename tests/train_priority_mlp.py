@@ -1,10 +1,12 @@
 """Train the vertex-priority network on the GPU and write its parameter file.
 
 Training set: R-MAT-G graphs (quadrants 0.45/0.15/0.15/0.25, edge factor 8,
-Sec. 4.1), scales 14 to 18 in turn, seeds 10000 + i.  Target of each vertex:
-log2(1 + its position in the smallest-last ordering) (Matula and Beck; one of
-the orderings the paper cites for Greedy, Sec. 1 and Sec. 3.1), computed by
-the oracle.  Features are computed by the library's GPU kernel
+Sec. 4.1), scales 14 to 18 in turn, seeds 10000 + i.  Labels: the oracle
+computes both orderings the paper cites for Greedy (Sec. 1, Sec. 3.1),
+smallest-last (Matula and Beck) and largest-first, colors the graph with
+serial Greedy in each, and the ordering that uses fewer colors (smallest-last
+on a tie) gives every vertex its target, log2(1 + its position in that
+ordering).  Features are computed by the library's GPU kernel
 and the network is trained by its GPU kernels (gc_mlp_train_step: fused
 gradient of the mean squared error, then Adam).
 
@@ -32,11 +34,12 @@ import graphgen as gg  # noqa: E402
 
 
 def _targets(job):
-    """Worker: smallest-last targets of one training graph (oracle, one thread)."""
+    """Worker: targets of one training graph and the ordering that labelled it
+    (oracle, one thread)."""
     scale, seed = job
     from oracle import learned as L
     g = gg.rmat(scale, 8, gg.RMAT_G, seed)
-    return L.smallest_last_targets(g.rowptr, g.colidx)
+    return L.ordering_targets(g.rowptr, g.colidx)
 
 
 def _greedy_colors(job):
@@ -77,7 +80,12 @@ def main():
     t0 = time.time()
     with ctx.Pool(a.workers) as pool:
         greedy_async = None if a.no_eval else pool.map_async(_greedy_colors, evals)
-        targets = pool.map(_targets, jobs, chunksize=1)
+        labelled = pool.map(_targets, jobs, chunksize=1)
+        targets = [t for t, _ in labelled]
+        labels = {"smallest_last": 0, "largest_first": 0}
+        for _, lab in labelled:
+            labels[lab["ordering"]] += 1
+        print("labels:", labels, flush=True)
         t_labels = time.time() - t0
         os.environ.pop("OMP_NUM_THREADS", None)
 
@@ -139,7 +147,10 @@ def main():
         "layout": "W1[32][6] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3 (float32)",
         "features": "L(deg), floor(log2(1+deg)), L(floor(sum nbr deg / deg)), L(max nbr deg), "
                     "L(sum nbr deg), L(min nbr deg); L = Mitchell log2(1+x), 16 fraction bits",
-        "target": "log2(1 + position in the smallest-last ordering) (smaller = colored earlier)",
+        "target": ("log2(1 + position in the ordering, smallest-last or largest-first (oracle), whose serial "
+                   "Greedy coloring of the graph uses fewer colors; smallest-last on a tie) "
+                   "(smaller = colored earlier)"),
+        "labels": labels,
         "training": {"graphs": a.graphs, "family": "R-MAT-G (0.45,0.15,0.15,0.25) edge factor 8",
                      "scales": [a.min_scale, a.max_scale], "seeds": [a.seed_base, a.seed_base + a.graphs - 1],
                      "samples": int(n), "epochs": a.epochs, "batch": a.batch, "lr": a.lr,
