@@ -62,9 +62,9 @@ typedef struct gc_options {
                                   most this many entries go 32 to a warp task
                                   (1..32, default 32) */
     int32_t medium_max_degree; /* active lists up to this length (and above
-                                  the small limit) go 8 to a warp task (1 when
-                                  that would leave warps idle), each list read
-                                  by the whole warp in turn; longer lists are
+                                  the small limit) go up to 16 to a warp task
+                                  (fewer in rounds with few of them), each list
+                                  read by the whole warp in turn; longer lists are
                                   split into chunks of 1024 entries, one warp
                                   each (small_max_degree..256, default 256) */
     int32_t max_rounds;        /* stop with GC_ERR_MAX_ROUNDS after this many

@@ -31,8 +31,9 @@
 // Work is split into warp-sized tasks, binned by the current active length:
 //   S bin (length <= s_max <= 32): 32 worklist entries per task, their lists
 //     walked as one flat range;
-//   M bin (s_max < length <= m_max <= 256): 8 worklist entries per task, each
-//     list read by the whole warp in turn (colors 1..64 in registers);
+//   M bin (s_max < length <= m_max <= 256): up to 16 worklist entries per
+//     task, each list read by the whole warp in turn (colors 1..64 in
+//     registers);
 //   H bin (length > m_max): one chunk of up to 1024 entries of one list per
 //     task; a list of one chunk is decided by its warp, and the chunks of a
 //     longer list OR their conflict flag and color windows into a per-vertex
@@ -70,7 +71,7 @@ constexpr int kPass1Flat = 256;               // pass 1: longer rows take the pe
 #define GC_MIN_BLOCKS 4
 #endif
 #ifndef GC_MED_PER_TASK
-#define GC_MED_PER_TASK 8
+#define GC_MED_PER_TASK 16
 #endif
 
 constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
@@ -125,6 +126,7 @@ struct RoundState {
     unsigned cnt[3][4];    // [k % 3] = {|U_k in S|, |U_k in M|, |U_k in H|, chunks of U_k in H}
     unsigned vol[3];       // [k % 3] = active entries round k reads
     unsigned defer_cnt;    // pass 1: vertices above kPass1Flat
+    alignas(128) unsigned task_next[3];  // [k % 3]: tasks of round k claimed so far (beyond the first two per warp)
     alignas(128) unsigned bar_count;
     alignas(128) unsigned bar_gen;
     alignas(128) int status;
@@ -1214,26 +1216,35 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 // One fused pass over U_k, shared among W warps (this warp is number gw).
 // Task t: first the H-bin chunks, then the M-bin entries kMedPerTask at a
 // time (one at a time when that still leaves warps idle), then the S-bin
-// entries 32 at a time (every task reads at most 1024 entries, so no warp
-// holds up the end of a round); warp gw takes t = gw, gw + W, ... and loads
-// the head of its next task before working on the current one.
+// entries 32 at a time (every task reads at most 1024 entries).  Warp gw
+// takes tasks gw and gw + W; then, with a counter (ctr), it claims one task
+// at a time (2W + the counter's old value), so that warps that drew cheap
+// tasks take more and the round ends when the work does, not when the
+// unluckiest warp's fixed share does; without one it takes gw + 2W, gw + 3W,
+// ...  The next task's head is loaded, and the claim after it issued, before
+// the current task runs, so neither waits on memory.
 template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
-                                         unsigned nHC, int& maxc, unsigned gw, unsigned W) {
+                                         unsigned nHC, int& maxc, unsigned gw, unsigned W, unsigned* ctr) {
     __shared__ FlatSmem s_flat[kWarpsPerBlockMax];
     const PassIO<T> io = pass_io(p, k);
     const unsigned wib = threadIdx.x >> 5;
     const unsigned tS = (nS + 31) / 32;
-    const unsigned mpt = nHC + nM + tS <= W ? 1u : (unsigned)kMedPerTask;
+    // M vertices per task: up to kMedPerTask when the round has enough of them
+    // for several tasks per warp, fewer (down to 1) as the round shrinks, so
+    // that a task's chain of per-vertex reads does not set the round's length
+    const unsigned mpt = max(1u, min((unsigned)kMedPerTask, nM / (4u * W)));
     const unsigned tM = (nM + mpt - 1) / mpt;
     const unsigned total = nHC + tM + tS;
     unsigned vol = 0;  // this lane's share of the next round's read volume
     TaskHead cur;
     if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM, mpt);
-    for (unsigned t = gw; t < total; t += W) {
-        const unsigned tn = t + W;
+    unsigned tn = gw + W;
+    for (unsigned t = gw; t < total;) {
         TaskHead nxt;
         if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
+        unsigned claim = 0;
+        if (ctr && tn < total && lane_id() == 0) claim = atomicAdd(ctr, 1u);
         if (t < nHC) {
             hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
 #if GC_M_WARP
@@ -1243,7 +1254,10 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         } else {
             flat_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
         }
+        const unsigned tnn = ctr ? 2u * W + __shfl_sync(kFull, claim, 0) : tn + W;
+        t = tn;
         cur = nxt;
+        tn = tn < total ? tnn : total;
     }
     fold_volume(p.st, p.round_vol, p.round_cap, k + 1, vol);
 }
@@ -1292,9 +1306,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
             unsigned* z = st->cnt[(k + 2) % 3];
             z[0] = z[1] = z[2] = z[3] = 0u;
             st->vol[(k + 2) % 3] = 0u;
+            st->task_next[(k + 1) % 3] = 0u;  // round k + 1's claims (no one touches it in round k)
             if (k - 1 < p.round_cap) p.round_sizes[k - 1] = (int32_t)size;
         }
-        run_pass<T, P>(p, k, nS, nM, nHC, maxc, gw, W);
+        run_pass<T, P>(p, k, nS, nM, nHC, maxc, gw, W, &st->task_next[k % 3]);
         if (tail) {
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1315,7 +1330,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) round_kernel(Params<T> p, int
                                                        unsigned nHC) {
     int maxc = 0;
     run_pass<T, P>(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-             (gridDim.x * blockDim.x) >> 5);
+             (gridDim.x * blockDim.x) >> 5, nullptr);
     fold_max_color(p.st, maxc);
 }
 
@@ -1342,7 +1357,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) graph_round_kernel(Params<T> 
     const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nHC = __ldcg(c + 3);
     int maxc = 0;
     run_pass<T, P>(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-             (gridDim.x * blockDim.x) >> 5);
+             (gridDim.x * blockDim.x) >> 5, nullptr);
     fold_max_color(st, maxc);
 }
 
