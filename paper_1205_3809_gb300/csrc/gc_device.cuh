@@ -971,6 +971,8 @@ __device__ __forceinline__ void vertex_task(const Params<T>& p, const PassIO<T>&
         }
         const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
         const uint32_t pv = (P && first) ? __ldg(p.prio + v) : 0u;
+        // v's static mask, word `lane` (read now, used after the list)
+        const uint32_t old = (lane < 8u && !first) ? __ldcg(p.stat + (size_t)v * 8 + lane) : 0u;
         if (lane < 8u) { sm.dyn[lane] = 0u; sm.stat[lane] = 0u; }
         __syncwarp();
         uint32_t rd0 = 0u, rs0 = 0u, rd1 = 0u, rs1 = 0u;  // this lane's colors 1..64 (all, settled)
@@ -1034,7 +1036,6 @@ __device__ __forceinline__ void vertex_task(const Params<T>& p, const PassIO<T>&
         const unsigned q7 = lane & 7u;
         uint32_t stat = 0u, all = 0u;
         if (lane < 8u) {
-            const uint32_t old = first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
             stat = old | sm.stat[q7] | (q7 == 0u ? rs0 : (q7 == 1u ? rs1 : 0u));
             all = stat | sm.dyn[q7] | (q7 == 0u ? rd0 : (q7 == 1u ? rd1 : 0u));
         }
@@ -1081,6 +1082,8 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
     const bool single = nch == 1;
     const uint32_t cv = word_color(ld_color(io.Xc + v, io.pol_col));
     const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
+    // a vertex decided by this warp: its static mask word `lane`, read now
+    const uint32_t old_single = (single && lane < 8u && !io.first) ? __ldcg(p.stat + (size_t)v * 8 + lane) : 0u;
     bool conflict = false;
     // this chunk's color windows: all colors in sm.dyn[0..8), settled ones in sm.stat[0..8)
     if (lane < 8u) { sm.dyn[lane] = 0u; sm.stat[lane] = 0u; }
@@ -1174,8 +1177,7 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
         conf = any_conflict;
         kept = (int32_t)local;
         if (lane < 8u) {
-            const uint32_t old = io.first ? 0u : __ldcg(p.stat + (size_t)v * 8 + lane);
-            stat = old | sword;
+            stat = old_single | sword;
             all = stat | word;
         }
     } else {
