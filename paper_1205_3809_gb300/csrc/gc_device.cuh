@@ -75,12 +75,6 @@ constexpr int kPass1Flat = 256;               // pass 1: longer rows take the pe
 #endif
 
 constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
-#ifndef GC_M_WARP
-#define GC_M_WARP 1
-#endif
-#ifndef GC_PREFETCH
-#define GC_PREFETCH 1   // L1 prefetch of the next M vertex's list and the next hub sub-block
-#endif
 constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task
 constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
@@ -757,9 +751,7 @@ struct FlatSmem {
 
 // Ask L1 for the line holding a (list entries read soon by this warp).
 __device__ __forceinline__ void prefetch_l1(const void* a) {
-#if GC_PREFETCH
     asm volatile("prefetch.global.L1 [%0];" :: "l"(a));
-#endif
 }
 
 // Stores of the next round's active lists and static masks: read once, in
@@ -936,7 +928,7 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     __syncwarp();
 }
 
-// M bin: up to 32 worklist entries per task (lane i holds entry i), taken
+// M bin: up to kMedPerTask worklist entries per task (lane i holds entry i), taken
 // one vertex at a time by the whole warp: lane l reads entries l, l + 32, ...
 // of the vertex's active list, four batches of 32 in flight.  Colors 1..64
 // collect in per-lane registers (all neighbours, and those found settled)
@@ -1216,9 +1208,9 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 }
 
 // One fused pass over U_k, shared among W warps (this warp is number gw).
-// Task t: first the H-bin chunks, then the M-bin entries kMedPerTask at a
-// time (one at a time when that still leaves warps idle), then the S-bin
-// entries 32 at a time (every task reads at most 1024 entries).  Warp gw
+// Task t: first the H-bin chunks, then the M-bin entries, up to kMedPerTask
+// per task (fewer as the round shrinks), then the S-bin entries 32 at a time
+// (an S or H task reads at most 1024 entries).  Warp gw
 // takes tasks gw and gw + W; then, with a counter (ctr), it claims one task
 // at a time (2W + the counter's old value), so that warps that drew cheap
 // tasks take more and the round ends when the work does, not when the
@@ -1249,10 +1241,8 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         if (ctr && tn < total && lane_id() == 0) claim = atomicAdd(ctr, 1u);
         if (t < nHC) {
             hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
-#if GC_M_WARP
         } else if (t - nHC < tM) {
             vertex_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
-#endif
         } else {
             flat_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
         }
