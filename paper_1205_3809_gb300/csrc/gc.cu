@@ -306,21 +306,22 @@ int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_
         return GC_OK;
     }
     // loop_mode 1: the host reads |U_k| after each pass
-    unsigned* h = nullptr;
     size_t have = dc.host_bytes;
     int rc = ensure_host(&dc.host, &have, 4096);
     if (rc != GC_OK) return rc;
     dc.host_bytes = have;
-    // pinned slots: h[0..3] counts read back, hs[0] size, hs[1] status, hs[2] rounds;
-    // every iteration synchronises the stream before a slot is rewritten
-    h = (unsigned*)dc.host;
-    int32_t* hs = (int32_t*)(h + 8);
+    // pinned slots: a copy of one round's counts read back, then hs[0] size, hs[1]
+    // status, hs[2] rounds; every iteration synchronises the stream before a slot
+    // is rewritten
+    static_assert(sizeof(gc::RoundCounts) + 16 <= 4096, "staging slots");
+    gc::RoundCounts* h = (gc::RoundCounts*)dc.host;
+    int32_t* hs = (int32_t*)((char*)dc.host + sizeof(gc::RoundCounts));
     RoundState* st = p.st;
     int k = 2;
     for (;; ++k) {
-        GC_CUDA(cudaMemcpyAsync(h, st->cnt[k % 3], 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(h, &st->rc[k % 3], sizeof(gc::RoundCounts), cudaMemcpyDeviceToHost, s));
         GC_CUDA(cudaStreamSynchronize(s));
-        const unsigned nS = h[0], nM = h[1], nH = h[2], nHC = h[3];
+        const unsigned nS = h->s, nM = h->m, nH = gc::hub_count(h->hc), nHC = gc::hub_chunks(h->hc);
         const unsigned size = nS + nM + nH;
         if (size == 0) break;
         if (k > p.max_rounds) {
@@ -333,7 +334,7 @@ int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_
             GC_CUDA(cudaMemcpyAsync(p.round_sizes + (k - 1), &hs[0], sizeof(int32_t),
                                     cudaMemcpyHostToDevice, s));
         }
-        GC_CUDA(cudaMemsetAsync(st->cnt[(k + 2) % 3], 0, 4 * sizeof(unsigned), s));
+        GC_CUDA(cudaMemsetAsync(&st->rc[(k + 2) % 3], 0, sizeof(gc::RoundCounts), s));
         const int64_t tasks = (int64_t)nHC + (nM + gc::kMedPerTask - 1) / gc::kMedPerTask + (nS + 31) / 32;
         const int64_t warps_per_block = threads / 32;
         const int grid = (int)std::max<int64_t>(

@@ -113,13 +113,27 @@ struct Stats {
     unsigned long long hub_chunks;  // sum over degree > m_max of ceil(degree / kChunk)
 };
 
+// One round's worklist counters.  Every warp appends through them, so each
+// sits on its own 128-byte line (its own L2 slice): on one line, the atomics
+// of all bins queued at one slice, which then served a quarter more requests
+// than any other.  A hub's two counters (its worklist position and its first
+// chunk) share one 64-bit word, taken with one atomic.
+struct RoundCounts {
+    alignas(128) unsigned s;               // |U_k in S|
+    alignas(128) unsigned m;               // |U_k in M|
+    alignas(128) unsigned long long hc;    // |U_k in H| (bits 0..31) | chunks of U_k in H (bits 32..63)
+    alignas(128) unsigned vol;             // active entries round k reads
+};
+
+__host__ __device__ __forceinline__ unsigned hub_count(unsigned long long hc) { return (unsigned)hc; }
+__host__ __device__ __forceinline__ unsigned hub_chunks(unsigned long long hc) { return (unsigned)(hc >> 32); }
+
 // The append counters, the two barrier words and the result words sit on
 // separate 128-byte lines, so that blocks polling the barrier do not slow
 // down the atomics of blocks still working.
 struct RoundState {
-    unsigned cnt[3][4];    // [k % 3] = {|U_k in S|, |U_k in M|, |U_k in H|, chunks of U_k in H}
-    unsigned vol[3];       // [k % 3] = active entries round k reads
-    unsigned defer_cnt;    // pass 1: vertices above kPass1Flat
+    RoundCounts rc[3];     // [k % 3]: the counts of U_k
+    alignas(128) unsigned defer_cnt;  // pass 1: vertices above kPass1Flat
     alignas(128) unsigned task_next[3];  // [k % 3]: tasks of round k claimed so far (beyond the first two per warp)
     alignas(128) unsigned bar_count;
     alignas(128) unsigned bar_gen;
@@ -283,7 +297,7 @@ __device__ __forceinline__ void warp_append_i32(bool flag, int32_t v, int32_t* l
 // Where the next round's worklists go.
 struct NextLists {
     int4* S; int4* M; int4* H; int32_t* Hc; int32_t* O;
-    unsigned* cnt;  // {S, M, H, H chunks} of the next round
+    RoundCounts* cnt;  // the next round's counts
     int32_t s_max, m_max;
 };
 
@@ -297,8 +311,9 @@ __device__ __forceinline__ void warp_append_hub(const NextLists& nl, int4 e) {
     const unsigned nch = (unsigned)(e.z + kChunk - 1) / kChunk;
     unsigned pos = 0, c0 = 0;
     if (lane_id() == 0) {
-        pos = atomicAdd(&nl.cnt[kBinH], 1u);
-        c0 = atomicAdd(&nl.cnt[3], nch);
+        const unsigned long long old = atomicAdd(&nl.cnt->hc, ((unsigned long long)nch << 32) | 1ull);
+        pos = hub_count(old);
+        c0 = hub_chunks(old);
         nl.H[pos] = e;
         nl.Hc[pos] = (int32_t)c0;
     }
@@ -314,7 +329,7 @@ __device__ __forceinline__ void warp_append_one(const NextLists& nl, int4 e) {
         warp_append_hub(nl, e);
     } else if (lane_id() == 0) {
         int4* list = bin == kBinM ? nl.M : nl.S;
-        list[atomicAdd(&nl.cnt[bin], 1u)] = e;
+        list[atomicAdd(bin == kBinM ? &nl.cnt->m : &nl.cnt->s, 1u)] = e;
     }
 }
 
@@ -439,13 +454,13 @@ __device__ __forceinline__ void fold_max_color(RoundState* st, int maxc) {
     if (lane_id() == 0 && m > 0) atomicMax(&st->max_color, m);
 }
 
-// Add a warp's share of round r's read volume to the round counter (vol[r % 3])
-// and to the telemetry (round_vol[r-1]).
+// Add a warp's share of round r's read volume to the round counter
+// (rc[r % 3].vol) and to the telemetry (round_vol[r-1]).
 __device__ __forceinline__ void fold_volume(RoundState* st, unsigned long long* round_vol, int32_t cap, int r,
                                             unsigned vol) {
     const unsigned s = __reduce_add_sync(kFull, vol);
     if (lane_id() == 0 && s) {
-        atomicAdd(&st->vol[r % 3], s);
+        atomicAdd(&st->rc[r % 3].vol, s);
         if (r - 1 < cap) atomicAdd(&round_vol[r - 1], (unsigned long long)s);
     }
 }
@@ -513,7 +528,7 @@ template <typename T>
 __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
     NextLists nl;
     nl.S = p.SA; nl.M = p.MA; nl.H = p.HA; nl.Hc = p.HcA; nl.O = p.OA;
-    nl.cnt = p.st->cnt[2];
+    nl.cnt = &p.st->rc[2];
     nl.s_max = p.s_max;
     nl.m_max = p.m_max;
     return nl;
@@ -594,8 +609,8 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin
         const int bin = bin_of(d, p.s_max, p.m_max);
         const bool go = valid && !longrow && hit;
         const int4 e = make_int4(v, b, d, d);
-        warp_append(go && bin == kBinS, e, nl.S, &nl.cnt[kBinS]);
-        warp_append(go && bin == kBinM, e, nl.M, &nl.cnt[kBinM]);
+        warp_append(go && bin == kBinS, e, nl.S, &nl.cnt->s);
+        warp_append(go && bin == kBinM, e, nl.M, &nl.cnt->m);
         // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
         unsigned hubs = __ballot_sync(kFull, go && bin == kBinH);
         while (hubs) {
@@ -686,7 +701,7 @@ __device__ __forceinline__ PassIO<T> pass_io(const Params<T>& p, int k) {
     io.next.H = odd ? p.HA : p.HB;
     io.next.Hc = odd ? p.HcA : p.HcB;
     io.next.O = odd ? p.OA : p.OB;
-    io.next.cnt = p.st->cnt[(k + 1) % 3];
+    io.next.cnt = &p.st->rc[(k + 1) % 3];
     io.next.s_max = p.s_max;
     io.next.m_max = p.m_max;
     io.pol_row = policy_evict_first();
@@ -923,8 +938,8 @@ __device__ __forceinline__ void flat_task(const Params<T>& p, const PassIO<T>& i
     // next round: same row start, `kept` active entries; the bin may shrink
     const int4 ne = make_int4(v, b, kept, en.w);
     const int nb = bin_of(kept, p.s_max, p.m_max);
-    warp_append(conflict && nb == kBinS, ne, io.next.S, &io.next.cnt[kBinS]);
-    warp_append(conflict && nb == kBinM, ne, io.next.M, &io.next.cnt[kBinM]);
+    warp_append(conflict && nb == kBinS, ne, io.next.S, &io.next.cnt->s);
+    warp_append(conflict && nb == kBinM, ne, io.next.M, &io.next.cnt->m);
     __syncwarp();
 }
 
@@ -1052,8 +1067,8 @@ __device__ __forceinline__ void vertex_task(const Params<T>& p, const PassIO<T>&
     // next round: same row start, the kept entries; the bin may shrink (never grow)
     const int4 ne = make_int4(en.x, en.y, my_kept, en.w);
     const int nb = bin_of(my_kept, p.s_max, p.m_max);
-    warp_append(my_conflict && nb == kBinS, ne, io.next.S, &io.next.cnt[kBinS]);
-    warp_append(my_conflict && nb == kBinM, ne, io.next.M, &io.next.cnt[kBinM]);
+    warp_append(my_conflict && nb == kBinS, ne, io.next.S, &io.next.cnt->s);
+    warp_append(my_conflict && nb == kBinM, ne, io.next.M, &io.next.cnt->m);
     __syncwarp();
 }
 
@@ -1210,13 +1225,15 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 // One fused pass over U_k, shared among W warps (this warp is number gw).
 // Task t: first the H-bin chunks, then the M-bin entries, up to kMedPerTask
 // per task (fewer as the round shrinks), then the S-bin entries 32 at a time
-// (an S or H task reads at most 1024 entries).  Warp gw
-// takes tasks gw and gw + W; then, with a counter (ctr), it claims one task
-// at a time (2W + the counter's old value), so that warps that drew cheap
-// tasks take more and the round ends when the work does, not when the
-// unluckiest warp's fixed share does; without one it takes gw + 2W, gw + 3W,
-// ...  The next task's head is loaded, and the claim after it issued, before
-// the current task runs, so neither waits on memory.
+// (an S or H task reads at most 1024 entries).  Warp gw takes tasks gw,
+// gw + W, ... for half of its even share (at least two); then, with a
+// counter (ctr), it claims one task at a time (nstat W + the counter's old
+// value), so that warps that drew cheap tasks take more and the round ends
+// when the work does, not when the unluckiest warp's fixed share does, while
+// only about half the tasks cost an atomic on the counter's line; without a
+// counter it keeps taking every W-th task.  The next task's head is loaded,
+// and the claim after it issued, before the current task runs, so neither
+// waits on memory.
 template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc, unsigned gw, unsigned W, unsigned* ctr) {
@@ -1231,14 +1248,19 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
     const unsigned tM = (nM + mpt - 1) / mpt;
     const unsigned total = nHC + tM + tS;
     unsigned vol = 0;  // this lane's share of the next round's read volume
+    // this warp's tasks: gw + jW for j < nstat, then claimed ones from nstat W on
+    const unsigned nstat = ctr ? max(2u, total / W / 2) : 0xffffffffu;
     TaskHead cur;
     if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM, mpt);
     unsigned tn = gw + W;
-    for (unsigned t = gw; t < total;) {
+    unsigned j = 0;  // position of the current task in that sequence
+    for (unsigned t = gw; t < total; ++j) {
         TaskHead nxt;
         if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
+        // the task after next: fixed, or claimed now (its number is needed after this task)
+        const bool fixed = j + 2u < nstat;
         unsigned claim = 0;
-        if (ctr && tn < total && lane_id() == 0) claim = atomicAdd(ctr, 1u);
+        if (!fixed && tn < total && lane_id() == 0) claim = atomicAdd(ctr, 1u);
         if (t < nHC) {
             hub_chunk<T, P>(p, io, cur, s_flat[wib], maxc, vol);
         } else if (t - nHC < tM) {
@@ -1246,7 +1268,7 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
         } else {
             flat_task<T, P>(p, io, cur.e, s_flat[wib], maxc, vol);
         }
-        const unsigned tnn = ctr ? 2u * W + __shfl_sync(kFull, claim, 0) : tn + W;
+        const unsigned tnn = fixed ? tn + W : nstat * W + __shfl_sync(kFull, claim, 0);
         t = tn;
         cur = nxt;
         tn = tn < total ? tnn : total;
@@ -1268,9 +1290,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
     unsigned W = (gridDim.x * blockDim.x) >> 5;
     bool tail = false;
     for (int k = 2;; ++k) {
-        const unsigned* c = st->cnt[k % 3];
-        const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nH = __ldcg(c + 2),
-                       nHC = __ldcg(c + 3);
+        const RoundCounts& c = st->rc[k % 3];
+        const unsigned long long hc = __ldcg(&c.hc);
+        const unsigned nS = __ldcg(&c.s), nM = __ldcg(&c.m), nH = hub_count(hc), nHC = hub_chunks(hc);
         const unsigned size = nS + nM + nH;
         // start of this pass (the last record, for the empty round, marks the end)
         if (p.round_ns && blockIdx.x == 0 && threadIdx.x == 0 && k - 1 <= p.round_cap)
@@ -1288,16 +1310,16 @@ __global__ void __launch_bounds__(256, kMinBlocks) rounds_persistent_kernel(Para
             }
             break;
         }
-        if (!tail && p.tail_volume >= 0 && __ldcg(&st->vol[k % 3]) <= (unsigned)p.tail_volume) {
+        if (!tail && p.tail_volume >= 0 && __ldcg(&st->rc[k % 3].vol) <= (unsigned)p.tail_volume) {
             if (blockIdx.x != 0) break;
             tail = true;
             gw = threadIdx.x >> 5;
             W = blockDim.x >> 5;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            unsigned* z = st->cnt[(k + 2) % 3];
-            z[0] = z[1] = z[2] = z[3] = 0u;
-            st->vol[(k + 2) % 3] = 0u;
+            RoundCounts& z = st->rc[(k + 2) % 3];
+            z.s = z.m = z.vol = 0u;
+            z.hc = 0ull;
             st->task_next[(k + 1) % 3] = 0u;  // round k + 1's claims (no one touches it in round k)
             if (k - 1 < p.round_cap) p.round_sizes[k - 1] = (int32_t)size;
         }
@@ -1345,8 +1367,8 @@ template <typename T, bool P>  // P: a priority array is given
 __global__ void __launch_bounds__(256, kMinBlocks) graph_round_kernel(Params<T> p) {
     RoundState* st = p.st;
     const int k = __ldcg(&st->graph_round);
-    const unsigned* c = st->cnt[k % 3];
-    const unsigned nS = __ldcg(c + 0), nM = __ldcg(c + 1), nHC = __ldcg(c + 3);
+    const RoundCounts& c = st->rc[k % 3];
+    const unsigned nS = __ldcg(&c.s), nM = __ldcg(&c.m), nHC = hub_chunks(__ldcg(&c.hc));
     int maxc = 0;
     run_pass<T, P>(p, k, nS, nM, nHC, maxc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
              (gridDim.x * blockDim.x) >> 5, nullptr);
@@ -1360,8 +1382,8 @@ __global__ void graph_cond_kernel(Params<T> p, int before_loop, cudaGraphConditi
     RoundState* st = p.st;
     const int k = before_loop ? 1 : st->graph_round;
     const int kn = k + 1;
-    const unsigned* c = st->cnt[kn % 3];
-    const unsigned size = c[0] + c[1] + c[2];
+    const RoundCounts& c = st->rc[kn % 3];
+    const unsigned size = c.s + c.m + hub_count(c.hc);
     unsigned go = 0u;
     if (size == 0u) {
         st->rounds = k;
@@ -1371,9 +1393,9 @@ __global__ void graph_cond_kernel(Params<T> p, int before_loop, cudaGraphConditi
         st->rounds = k;
         st->status = kStatusMaxRounds;
     } else {
-        unsigned* z = st->cnt[(kn + 1) % 3];
-        z[0] = z[1] = z[2] = z[3] = 0u;
-        st->vol[(kn + 1) % 3] = 0u;
+        RoundCounts& z = st->rc[(kn + 1) % 3];
+        z.s = z.m = z.vol = 0u;
+        z.hc = 0ull;
         if (kn - 1 < p.round_cap) p.round_sizes[kn - 1] = (int32_t)size;
         st->graph_round = kn;
         go = 1u;
