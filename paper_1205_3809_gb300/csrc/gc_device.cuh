@@ -29,8 +29,8 @@
 // overflow status and the host reruns with 32-bit state.
 //
 // Work is split into warp-sized tasks, binned by the current active length:
-//   S bin (length <= s_max <= 32): 32 worklist entries per task, their lists
-//     walked as one flat range;
+//   S bin (length <= s_max <= 32): 32 worklist entries per task (down to 4
+//     in the small rounds at the end), their lists walked as one flat range;
 //   M bin (s_max < length <= m_max <= 256): up to 16 worklist entries per
 //     task, each list read by the whole warp in turn (colors 1..64 in
 //     registers);
@@ -76,6 +76,7 @@ constexpr int kPass1Flat = 256;               // pass 1: longer rows take the pe
 
 constexpr int kFlatBatches = GC_FLAT_BATCHES;  // flat tasks: batches in flight together
 constexpr int kMedPerTask = GC_MED_PER_TASK;   // M-bin vertices per task
+constexpr int kShortPerTaskMin = 4;            // S-bin vertices per task in a small round
 constexpr int kMinBlocks = GC_MIN_BLOCKS;      // round kernels: blocks per SM the registers allow
 constexpr int kWarpsPerBlockMax = 8;          // blocks of <= 256 threads
 
@@ -735,7 +736,8 @@ struct TaskHead {
 
 template <typename T>
 __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, unsigned nS,
-                                              unsigned nM, unsigned nHC, unsigned tM, unsigned mpt) {
+                                              unsigned nM, unsigned nHC, unsigned tM, unsigned mpt,
+                                              unsigned spt) {
     TaskHead h;
     h.pos = 0;
     h.lo = 0;
@@ -747,8 +749,8 @@ __device__ __forceinline__ TaskHead load_head(const PassIO<T>& io, unsigned t, u
         const unsigned i = (t - nHC) * mpt + lane_id();
         h.e = (lane_id() < mpt && i < nM) ? __ldcg(io.M + i) : make_int4(-1, 0, 0, 0);
     } else {
-        const unsigned i = (t - nHC - tM) * 32 + lane_id();
-        h.e = i < nS ? __ldcg(io.S + i) : make_int4(-1, 0, 0, 0);
+        const unsigned i = (t - nHC - tM) * spt + lane_id();
+        h.e = (lane_id() < spt && i < nS) ? __ldcg(io.S + i) : make_int4(-1, 0, 0, 0);
     }
     return h;
 }
@@ -1224,8 +1226,9 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 
 // One fused pass over U_k, shared among W warps (this warp is number gw).
 // Task t: first the H-bin chunks, then the M-bin entries, up to kMedPerTask
-// per task (fewer as the round shrinks), then the S-bin entries 32 at a time
-// (an S or H task reads at most 1024 entries).  Warp gw takes tasks gw,
+// per task (fewer as the round shrinks), then the S-bin entries, 32 per task
+// (down to kShortPerTaskMin as the round shrinks; an S or H task reads at most
+// 1024 entries).  Warp gw takes tasks gw,
 // gw + W, ... for half of its even share (at least two); then, with a
 // counter (ctr), it claims one task at a time (nstat W + the counter's old
 // value), so that warps that drew cheap tasks take more and the round ends
@@ -1240,7 +1243,11 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
     __shared__ FlatSmem s_flat[kWarpsPerBlockMax];
     const PassIO<T> io = pass_io(p, k);
     const unsigned wib = threadIdx.x >> 5;
-    const unsigned tS = (nS + 31) / 32;
+    // S vertices per task: 32 in a large round, down to kShortPerTaskMin as it
+    // shrinks; a task of 32 short lists walks up to 1024 entries in sequence,
+    // which in the last rounds was the longest chain of the round
+    const unsigned spt = max((unsigned)kShortPerTaskMin, min(32u, nS / (4u * W)));
+    const unsigned tS = (nS + spt - 1) / spt;
     // M vertices per task: up to kMedPerTask when the round has enough of them
     // for several tasks per warp, fewer (down to 1) as the round shrinks, so
     // that a task's chain of per-vertex reads does not set the round's length
@@ -1251,12 +1258,12 @@ __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS,
     // this warp's tasks: gw + jW for j < nstat, then claimed ones from nstat W on
     const unsigned nstat = ctr ? max(2u, total / W / 2) : 0xffffffffu;
     TaskHead cur;
-    if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM, mpt);
+    if (gw < total) cur = load_head(io, gw, nS, nM, nHC, tM, mpt, spt);
     unsigned tn = gw + W;
     unsigned j = 0;  // position of the current task in that sequence
     for (unsigned t = gw; t < total; ++j) {
         TaskHead nxt;
-        if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt);
+        if (tn < total) nxt = load_head(io, tn, nS, nM, nHC, tM, mpt, spt);
         // the task after next: fixed, or claimed now (its number is needed after this task)
         const bool fixed = j + 2u < nstat;
         unsigned claim = 0;
