@@ -545,6 +545,10 @@ __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
 // pass1_long_kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin, int32_t v_end) {
+    // a warp takes two tasks (t, t + W) at a time and appends their S and M
+    // entries with one atomic per bin: every task appends to both, and the
+    // counters' lines were the busiest of the L2 in this kernel
+    constexpr int NT = 2;
     const unsigned lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -553,74 +557,100 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin
     const uint64_t pol_adj = policy_evict_first();
     int maxc = 0;
     unsigned vol = 0;
-    for (int64_t t = gw; t < ntasks; t += W) {
-        const int64_t vv = (int64_t)v_begin + t * 32 + lane;
-        const bool valid = vv < v_end;
-        const int32_t v = valid ? (int32_t)vv : 0;
-        const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
-        const int32_t d = valid ? __ldg(p.rowptr + v + 1) - b : 0;
-        const bool longrow = d > kPass1Flat;
-        const int32_t eff = longrow ? 0 : d;
-        const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
-        int32_t incl = eff;
+    for (int64_t t0 = gw; t0 < ntasks; t0 += W * NT) {
+        int4 ev[NT];
+        bool fS[NT], fM[NT];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t x = __shfl_up_sync(kFull, incl, o);
-            if ((int)lane >= o) incl += x;
-        }
-        const int32_t off = incl - eff;
-        const int32_t D = __shfl_sync(kFull, incl, 31);
-        bool hit = false;
-        for (int32_t F0 = 0; F0 < D; F0 += 32 * 4) {
-            int32_t w[4], own[4];
+        for (int jt = 0; jt < NT; ++jt) {
+            const int64_t t = t0 + (int64_t)jt * W;
+            const int64_t vv = (int64_t)v_begin + t * 32 + lane;
+            const bool valid = t < ntasks && vv < v_end;
+            const int32_t v = valid ? (int32_t)vv : 0;
+            const int32_t b = valid ? __ldg(p.rowptr + v) : 0;
+            const int32_t d = valid ? __ldg(p.rowptr + v + 1) - b : 0;
+            const bool longrow = d > kPass1Flat;
+            const int32_t eff = longrow ? 0 : d;
+            const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
+            int32_t incl = eff;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int32_t f = F0 + 32 * u + (int32_t)lane;
-                // first row whose running total exceeds f
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const int mid = (lo + hi) >> 1;
-                    const int32_t val = __shfl_sync(kFull, incl, mid);
-                    if (val > f) hi = mid; else lo = mid + 1;
-                }
-                own[u] = lo;
-                const int32_t ob = __shfl_sync(kFull, b, lo);
-                const int32_t oo = __shfl_sync(kFull, off, lo);
-                w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), pol_adj) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t x = __shfl_up_sync(kFull, incl, o);
+                if ((int)lane >= o) incl += x;
             }
+            const int32_t off = incl - eff;
+            const int32_t D = __shfl_sync(kFull, incl, 31);
+            bool hit = false;
+            for (int32_t F0 = 0; F0 < D; F0 += 32 * 4) {
+                int32_t w[4], own[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int32_t f = F0 + 32 * u + (int32_t)lane;
-                const uint32_t opv = __shfl_sync(kFull, pv, own[u]);
-                const bool h = f < D && precedes(p.prio, w[u], (int32_t)(v_begin + t * 32 + own[u]), opv);
-                const unsigned ballot = __ballot_sync(kFull, h);
-                const int32_t lo = max(0, min(32, off - (F0 + 32 * u)));
-                const int32_t hi = max(0, min(32, off + eff - (F0 + 32 * u)));
-                if (hi > lo) {
-                    const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
-                    if ((ballot >> lo) & bits) hit = true;
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t f = F0 + 32 * u + (int32_t)lane;
+                    // first row whose running total exceeds f
+                    int lo = 0, hi = 31;
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) {
+                        const int mid = (lo + hi) >> 1;
+                        const int32_t val = __shfl_sync(kFull, incl, mid);
+                        if (val > f) hi = mid; else lo = mid + 1;
+                    }
+                    own[u] = lo;
+                    const int32_t ob = __shfl_sync(kFull, b, lo);
+                    const int32_t oo = __shfl_sync(kFull, off, lo);
+                    w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), pol_adj) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t f = F0 + 32 * u + (int32_t)lane;
+                    const uint32_t opv = __shfl_sync(kFull, pv, own[u]);
+                    const bool h = f < D && precedes(p.prio, w[u], (int32_t)(v_begin + t * 32 + own[u]), opv);
+                    const unsigned ballot = __ballot_sync(kFull, h);
+                    const int32_t lo = max(0, min(32, off - (F0 + 32 * u)));
+                    const int32_t hi = max(0, min(32, off + eff - (F0 + 32 * u)));
+                    if (hi > lo) {
+                        const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
+                        if ((ballot >> lo) & bits) hit = true;
+                    }
                 }
             }
+            if (valid && !longrow) {
+                pass1_write(p, v, hit, maxc);
+                if (hit) vol += (unsigned)d;
+            }
+            const int bin = bin_of(d, p.s_max, p.m_max);
+            const bool go = valid && !longrow && hit;
+            ev[jt] = make_int4(v, b, d, d);
+            fS[jt] = go && bin == kBinS;
+            fM[jt] = go && bin == kBinM;
+            // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
+            unsigned hubs = __ballot_sync(kFull, go && bin == kBinH);
+            while (hubs) {
+                const int j = __ffs(hubs) - 1;
+                hubs &= hubs - 1;
+                const int32_t dj = __shfl_sync(kFull, d, j);
+                warp_append_hub(nl, make_int4(__shfl_sync(kFull, v, j), __shfl_sync(kFull, b, j), dj, dj));
+            }
+            warp_append_i32(valid && longrow, v, p.defer, &p.st->defer_cnt);
         }
-        if (valid && !longrow) {
-            pass1_write(p, v, hit, maxc);
-            if (hit) vol += (unsigned)d;
+        // the S and M entries of these NT tasks, one atomic per bin
+#pragma unroll
+        for (int bin = 0; bin < 2; ++bin) {
+            unsigned bal[NT], n = 0;
+#pragma unroll
+            for (int jt = 0; jt < NT; ++jt) {
+                bal[jt] = __ballot_sync(kFull, bin == 0 ? fS[jt] : fM[jt]);
+                n += __popc(bal[jt]);
+            }
+            if (n == 0) continue;
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(bin == 0 ? &nl.cnt->s : &nl.cnt->m, n);
+            base = __shfl_sync(kFull, base, 0);
+            int4* const list = bin == 0 ? nl.S : nl.M;
+#pragma unroll
+            for (int jt = 0; jt < NT; ++jt) {
+                if ((bal[jt] >> lane) & 1u) list[base + __popc(bal[jt] & ((1u << lane) - 1u))] = ev[jt];
+                base += __popc(bal[jt]);
+            }
         }
-        const int bin = bin_of(d, p.s_max, p.m_max);
-        const bool go = valid && !longrow && hit;
-        const int4 e = make_int4(v, b, d, d);
-        warp_append(go && bin == kBinS, e, nl.S, &nl.cnt->s);
-        warp_append(go && bin == kBinM, e, nl.M, &nl.cnt->m);
-        // hubs that stayed in the flat range (m_max < d <= kPass1Flat)
-        unsigned hubs = __ballot_sync(kFull, go && bin == kBinH);
-        while (hubs) {
-            const int j = __ffs(hubs) - 1;
-            hubs &= hubs - 1;
-            const int32_t dj = __shfl_sync(kFull, d, j);
-            warp_append_hub(nl, make_int4(__shfl_sync(kFull, v, j), __shfl_sync(kFull, b, j), dj, dj));
-        }
-        warp_append_i32(valid && longrow, v, p.defer, &p.st->defer_cnt);
     }
     fold_max_color(p.st, maxc);
     fold_volume(p.st, p.round_vol, p.round_cap, 2, vol);
