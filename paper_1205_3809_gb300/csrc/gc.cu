@@ -287,7 +287,7 @@ int run_rounds_p(const gc_options& o, DeviceCache& dc, Params<T>& p, cudaStream_
             GC_CUDA(cudaGetLastError());
             *launches += 1;
         }
-        gc::pass1_long_kernel<T><<<dc.sms * 2, 256, 0, s>>>(p);
+        gc::pass1_long_kernel<T><<<dc.sms * gc::kPass1LongBlocksPerSm, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
         *launches += 1;
         if (o.telemetry) GC_CUDA(cudaEventRecord(dc.ev[2], s));
@@ -963,7 +963,7 @@ int batch_enqueue_typed(gc_batch& b, cudaStream_t s) {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b.sms * 8));
         gc::pass1_kernel<T><<<grid, 256, 0, s>>>(p, 0, (int32_t)b.N);
         GC_CUDA(cudaGetLastError());
-        gc::pass1_long_kernel<T><<<b.sms * 2, 256, 0, s>>>(p);
+        gc::pass1_long_kernel<T><<<b.sms * gc::kPass1LongBlocksPerSm, 256, 0, s>>>(p);
         GC_CUDA(cudaGetLastError());
         launches += 2;
     }

@@ -64,6 +64,7 @@ constexpr int kMedMaxLimit = 32 * kPerLane;   // M bin: length <= 256
 constexpr int kHubSub = 32 * kPerLane;        // 256 entries: one sub-block of a hub chunk
 constexpr int kChunk = 4 * kHubSub;           // 1024 entries per H-bin task
 constexpr int kPass1Flat = 256;               // pass 1: longer rows take the per-warp path
+constexpr int kPass1LongBlocksPerSm = 8;      // pass 1, long rows: grid of 8 blocks per SM
 #ifndef GC_FLAT_BATCHES
 #define GC_FLAT_BATCHES 4
 #endif
@@ -321,6 +322,32 @@ __device__ __forceinline__ void warp_append_hub(const NextLists& nl, int4 e) {
     pos = __shfl_sync(kFull, pos, 0);
     c0 = __shfl_sync(kFull, c0, 0);
     for (unsigned j = lane_id(); j < nch; j += 32) nl.O[c0 + j] = (int32_t)pos;
+}
+
+// Append the H-bin entries of the lanes whose flag is set, with one atomic for
+// all of them (their chunks get consecutive ranges).  Called by all lanes.
+__device__ __forceinline__ void warp_append_hubs(const NextLists& nl, bool flag, int4 e) {
+    const unsigned ballot = __ballot_sync(kFull, flag);
+    if (ballot == 0) return;
+    const unsigned lane = lane_id();
+    const unsigned nch = flag ? (unsigned)(e.z + kChunk - 1) / kChunk : 0u;
+    unsigned incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += x;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(&nl.cnt->hc, ((unsigned long long)total << 32) | (unsigned long long)__popc(ballot));
+    old = __shfl_sync(kFull, old, 0);
+    if (flag) {
+        const unsigned pos = hub_count(old) + (unsigned)__popc(ballot & ((1u << lane) - 1u));
+        const unsigned c0 = hub_chunks(old) + incl - nch;
+        nl.H[pos] = e;
+        nl.Hc[pos] = (int32_t)c0;
+        for (unsigned j = 0; j < nch; ++j) nl.O[c0 + j] = (int32_t)pos;
+    }
 }
 
 // Append one entry held by lane 0 (any bin).  Called by all lanes of a warp.
@@ -656,8 +683,11 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin
     fold_volume(p.st, p.round_vol, p.round_cap, 2, vol);
 }
 
-// Round 1 for rows longer than kPass1Flat: one warp per vertex, 128
-// entries per step, stop at the first preceding neighbour.
+// Round 1 for rows longer than kPass1Flat: a warp takes up to 32 of them (one
+// per lane; fewer when there are not many, so that every warp has some),
+// reads them one after another, 128 entries per step, stopping at the first
+// preceding neighbour, and appends the conflicting ones (all H bin: longer
+// than kPass1Flat >= m_max) with one atomic.
 template <typename T>
 __global__ void __launch_bounds__(256) pass1_long_kernel(Params<T> p) {
     const unsigned lane = lane_id();
@@ -668,28 +698,38 @@ __global__ void __launch_bounds__(256) pass1_long_kernel(Params<T> p) {
     const uint64_t pol_adj = policy_evict_first();
     int maxc = 0;
     unsigned vol = 0;
-    for (int64_t t = gw; t < nd; t += W) {
-        const int32_t v = __ldcg(p.defer + t);
-        const int32_t b = __ldg(p.rowptr + v), e = __ldg(p.rowptr + v + 1);
-        const uint32_t pv = p.prio ? __ldg(p.prio + v) : 0u;
-        bool conflict = false;
-        for (int32_t c = b; c < e && !conflict; c += 128) {
-            int32_t w[4];
+    const int64_t R = max((int64_t)1, min((int64_t)32, ((int64_t)nd + W - 1) / W));  // rows per warp
+    for (int64_t t0 = gw * R; t0 < nd; t0 += W * R) {
+        const int64_t i = t0 + lane;
+        const bool valid = lane < R && i < nd;
+        const int32_t v = valid ? __ldcg(p.defer + i) : 0;
+        const int32_t b = valid ? __ldg(p.rowptr + v) : 0, e = valid ? __ldg(p.rowptr + v + 1) : 0;
+        const uint32_t pv = (p.prio && valid) ? __ldg(p.prio + v) : 0u;
+        bool mine = false;
+        const int rows = (int)min(R, (int64_t)nd - t0);
+        for (int j = 0; j < rows; ++j) {
+            const int32_t vj = __shfl_sync(kFull, v, j), bj = __shfl_sync(kFull, b, j), ej = __shfl_sync(kFull, e, j);
+            const uint32_t pvj = __shfl_sync(kFull, pv, j);
+            bool conflict = false;
+            for (int32_t c = bj; c < ej && !conflict; c += 128) {
+                int32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int32_t i = c + 32 * u + (int32_t)lane;
-                w[u] = i < e ? ld_adj(p.colidx + i, pol_adj) : -1;
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t x = c + 32 * u + (int32_t)lane;
+                    w[u] = x < ej ? ld_adj(p.colidx + x, pol_adj) : -1;
+                }
+                bool h = false;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) h |= w[u] >= 0 && precedes(p.prio, w[u], vj, pvj);
+                conflict = __any_sync(kFull, h);
             }
-            bool h = false;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) h |= w[u] >= 0 && precedes(p.prio, w[u], v, pv);
-            conflict = __any_sync(kFull, h);
+            if ((int)lane == j) mine = conflict;
         }
-        if (lane == 0) pass1_write(p, v, conflict, maxc);
-        if (conflict) {
-            if (lane == 0) vol += (unsigned)(e - b);
-            warp_append_one(nl, make_int4(v, b, e - b, e - b));
+        if (valid) {
+            pass1_write(p, v, mine, maxc);
+            if (mine) vol += (unsigned)(e - b);
         }
+        warp_append_hubs(nl, valid && mine, make_int4(v, b, e - b, e - b));
     }
     fold_max_color(p.st, maxc);
     fold_volume(p.st, p.round_vol, p.round_cap, 2, vol);
