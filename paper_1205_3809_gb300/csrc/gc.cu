@@ -5,10 +5,12 @@
 //      checks; one device-to-host copy decides the color width (16-bit color
 //      state when every first-fit color fits, i.e. max degree + 1 <= 65535)
 //      and sizes the workspace;
-//   2. pass1_thread_kernel + pass1_big_kernel: round 1 (closed form, all
-//      colors 1), its conflict test, and round 2's colors (all 2);
+//   2. pass1_kernel (rows of up to 256 entries) + pass1_long_kernel (longer
+//      rows): round 1 (closed form, all colors 1), its conflict test, and
+//      round 2's colors (all 2);
 //   3. rounds_persistent_kernel: every later round in one cooperative launch
-//      (or, with loop_mode = 1, one round_kernel launch per round);
+//      (or, with loop_mode = 1, one round_kernel launch per round; with
+//      loop_mode = 2, graph_round_kernel in a CUDA graph's conditional loop);
 //   4. one device-to-host copy of the round state and telemetry.
 #include <cuda_runtime.h>
 

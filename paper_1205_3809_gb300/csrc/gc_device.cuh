@@ -63,7 +63,7 @@ constexpr int kSmallMaxLimit = 32;            // S bin: length <= 32
 constexpr int kMedMaxLimit = 32 * kPerLane;   // M bin: length <= 256
 constexpr int kHubSub = 32 * kPerLane;        // 256 entries: one sub-block of a hub chunk
 constexpr int kChunk = 4 * kHubSub;           // 1024 entries per H-bin task
-constexpr int kPass1Flat = 256;               // pass 1: longer rows take the per-warp path
+constexpr int kPass1Flat = 256;               // pass 1: longer rows go to pass1_long_kernel
 constexpr int kPass1LongBlocksPerSm = 8;      // pass 1, long rows: grid of 8 blocks per SM
 #ifndef GC_FLAT_BATCHES
 #define GC_FLAT_BATCHES 4
