@@ -566,16 +566,22 @@ __device__ __forceinline__ NextLists pass1_next(const Params<T>& p) {
 // (v_begin a multiple of 32; the host may launch it per range as the input
 // arrives).  Their adjacency entries
 // (rows of degree <= kPass1Flat) are read as one flat, coalesced range;
-// lane l of batch u handles flat entry F0 + 32u + l, finds its row by a
-// binary search over the rows' running totals, and the per-row conflict
-// flag is gathered from the batch ballot.  Longer rows go to
-// pass1_long_kernel.
+// lane l of batch u handles flat entry F0 + 32u + l, finds its row from the
+// batch's row starts (an OR-reduction over the warp and a table of the
+// non-empty rows' lanes), and marks the row in shared memory when the entry
+// precedes it.  Longer rows go to pass1_long_kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin, int32_t v_end) {
+__global__ void __launch_bounds__(256, 5) pass1_kernel(Params<T> p, int32_t v_begin, int32_t v_end) {
     // a warp takes two tasks (t, t + W) at a time and appends their S and M
     // entries with one atomic per bin: every task appends to both, and the
     // counters' lines were the busiest of the L2 in this kernel
     constexpr int NT = 2;
+    struct P1Smem {
+        uint8_t lane_of[32];  // lane of the i-th non-empty row
+        unsigned hit[32];     // row r has a preceding neighbour
+    };
+    __shared__ P1Smem s_p1[8];
+    const unsigned wib = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -606,39 +612,38 @@ __global__ void __launch_bounds__(256) pass1_kernel(Params<T> p, int32_t v_begin
             }
             const int32_t off = incl - eff;
             const int32_t D = __shfl_sync(kFull, incl, 31);
-            bool hit = false;
+            // entry f's row: the last non-empty row starting at or before f, found
+            // from the batch's row starts (one OR-reduction) and a lane table
+            const unsigned nz = __ballot_sync(kFull, eff > 0);
+            if (eff > 0) s_p1[wib].lane_of[__popc(nz & ((1u << lane) - 1u))] = (uint8_t)lane;
+            s_p1[wib].hit[lane] = 0u;
+            const int32_t b_off = b - off;  // entry f of this row sits at colidx[b_off + f]
+            __syncwarp();
             for (int32_t F0 = 0; F0 < D; F0 += 32 * 4) {
                 int32_t w[4], own[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int32_t f = F0 + 32 * u + (int32_t)lane;
-                    // first row whose running total exceeds f
-                    int lo = 0, hi = 31;
-#pragma unroll
-                    for (int s = 0; s < 5; ++s) {
-                        const int mid = (lo + hi) >> 1;
-                        const int32_t val = __shfl_sync(kFull, incl, mid);
-                        if (val > f) hi = mid; else lo = mid + 1;
-                    }
-                    own[u] = lo;
-                    const int32_t ob = __shfl_sync(kFull, b, lo);
-                    const int32_t oo = __shfl_sync(kFull, off, lo);
-                    w[u] = f < D ? ld_adj(p.colidx + ob + (f - oo), pol_adj) : 0;
+                    const int32_t base = F0 + 32 * u;
+                    const int32_t f = base + (int32_t)lane;
+                    const int32_t rel = off - base;
+                    const unsigned before = __popc(__ballot_sync(kFull, eff > 0 && rel < 0));
+                    const unsigned starts = __reduce_or_sync(kFull, (eff > 0 && rel >= 0 && rel < 32) ? (1u << rel) : 0u);
+                    const unsigned rank = before + __popc(starts & (0xffffffffu >> (31 - lane)));
+                    const int o = (f < D && rank > 0) ? (int)s_p1[wib].lane_of[rank - 1] : 0;
+                    own[u] = o;
+                    const int32_t rb = __shfl_sync(kFull, b_off, o);
+                    w[u] = f < D ? ld_adj(p.colidx + rb + f, pol_adj) : 0;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int32_t f = F0 + 32 * u + (int32_t)lane;
                     const uint32_t opv = __shfl_sync(kFull, pv, own[u]);
-                    const bool h = f < D && precedes(p.prio, w[u], (int32_t)(v_begin + t * 32 + own[u]), opv);
-                    const unsigned ballot = __ballot_sync(kFull, h);
-                    const int32_t lo = max(0, min(32, off - (F0 + 32 * u)));
-                    const int32_t hi = max(0, min(32, off + eff - (F0 + 32 * u)));
-                    if (hi > lo) {
-                        const unsigned bits = hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u);
-                        if ((ballot >> lo) & bits) hit = true;
-                    }
+                    if (f < D && precedes(p.prio, w[u], (int32_t)(v_begin + t * 32 + own[u]), opv))
+                        s_p1[wib].hit[own[u]] = 1u;
                 }
             }
+            __syncwarp();
+            const bool hit = s_p1[wib].hit[lane] != 0u;
             if (valid && !longrow) {
                 pass1_write(p, v, hit, maxc);
                 if (hit) vol += (unsigned)d;
