@@ -117,6 +117,20 @@ def test_degrees_at_bin_edges(gcpkg):
     _check(gcpkg, g, options={"small_max_degree": 31, "medium_max_degree": 255})
 
 
+def test_many_long_rows(gcpkg):
+    """About 20,000 rows longer than 256 entries (G(20,000, 3M), average degree
+    300): round 1's long-row pass gives each warp several of them and appends
+    the conflicting ones with one atomic per warp; every later round runs on
+    hub chunks.  Index priority, random keys with many ties, and the per-round
+    launch form."""
+    g = gg.gnm(20000, 3000000, 11)
+    assert int((g.degrees > 256).sum()) > 19000
+    _check(gcpkg, g)
+    keys = (gg.draws(5, 9, g.n) >> np.uint64(56)).astype(np.uint32)
+    _check(gcpkg, g, prio=keys)
+    _check(gcpkg, g, options={"loop_mode": 1})
+
+
 def test_many_colors_window_rescan(gcpkg):
     """K_600: first-fit colors beyond the 64- and 256-wide mask windows."""
     res = _check(gcpkg, gg.complete(600))
