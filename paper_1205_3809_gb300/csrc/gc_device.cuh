@@ -1302,16 +1302,15 @@ __device__ __forceinline__ void hub_chunk(const Params<T>& p, const PassIO<T>& i
 // One fused pass over U_k, shared among W warps (this warp is number gw).
 // Task t: first the H-bin chunks, then the M-bin entries, up to kMedPerTask
 // per task (fewer as the round shrinks), then the S-bin entries, 32 per task
-// (down to kShortPerTaskMin as the round shrinks; an S or H task reads at most
-// 1024 entries).  Warp gw takes tasks gw,
-// gw + W, ... for half of its even share (at least two); then, with a
-// counter (ctr), it claims one task at a time (nstat W + the counter's old
-// value), so that warps that drew cheap tasks take more and the round ends
-// when the work does, not when the unluckiest warp's fixed share does, while
-// only about half the tasks cost an atomic on the counter's line; without a
-// counter it keeps taking every W-th task.  The next task's head is loaded,
-// and the claim after it issued, before the current task runs, so neither
-// waits on memory.
+// (down to kShortPerTaskMin as the round shrinks); an S or H task reads at
+// most 1024 entries.  Warp gw takes tasks gw, gw + W, ... for half of its even
+// share (at least two); then, with a counter (ctr), it claims one task at a
+// time (nstat W + the counter's old value), so that warps that drew cheap
+// tasks take more and the round ends when the work does, not when the
+// unluckiest warp's fixed share does, while only about half the tasks cost an
+// atomic on the counter's line; without a counter it keeps taking every W-th
+// task.  The next task's head is loaded, and the claim after it issued,
+// before the current task runs, so neither waits on memory.
 template <typename T, bool P>  // P: a priority array is given
 __device__ __forceinline__ void run_pass(const Params<T>& p, int k, unsigned nS, unsigned nM,
                                          unsigned nHC, int& maxc, unsigned gw, unsigned W, unsigned* ctr) {
